@@ -1,0 +1,113 @@
+"""Block-sparse two-site effective-Hamiltonian product (oracle; test infrastructure only).
+
+The DMRG update diagonalises H_eff on the two-site space with a Krylov solver
+(section "Theory of TNS/DMRG regarding error analysis": the second
+subroutine), and its matrix-vector product is built from binary tensor
+contractions done as matrix multiplications (same section, first
+subroutine).  With H_eff = sum_k c_k L_k (x) R_k acting on psi viewed as a
+(left enlarged) x (right enlarged) matrix, the product is
+    Y = sum_k c_k L_k psi R_k^T,
+and with U(1)xU(1) sector symmetry every factor is block sparse: the task
+(k, src, dst) adds c_k L_k[dst<-src] psi[src] R_k[dst<-src]^T to Y[dst].
+
+Functions:
+ * heff_apply_fp64     plain FP64, one numpy product per block (the error reference).
+ * heff_dense          the dense matrix sum_k c_k L_k (x) R_k on vec(psi), brute force
+                       (pins heff_apply_fp64 on tiny layouts).
+ * heff_apply_emulated the two-stage emulated definition: for every source sector
+                       one Ozaki product of the stacked L blocks with psi[src]; for
+                       every target sector one Ozaki product of the concatenated
+                       intermediates with the stacked (c_k R_k)^T.  Each stage is one
+                       exact emulated GEMM rounded once (see ``ozaki``).
+
+Parity: heff_apply_fp64 pinned by heff_dense (brute force) and Hermiticity;
+heff_apply_emulated pinned through ``ozaki`` and by its distance to
+heff_apply_fp64 staying inside the summed per-GEMM error bounds.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import ozaki
+
+
+def _blocks(psi_flat, st):
+    off = st.psi_offsets()
+    return [np.asarray(psi_flat[off[q]:off[q + 1]], dtype=np.float64).reshape(int(st.m[q]), int(st.n[q]))
+            for q in range(st.nsec)]
+
+
+def _flat(blocks):
+    return np.concatenate([b.reshape(-1) for b in blocks]) if blocks else np.zeros(0)
+
+
+def heff_apply_fp64(st, Lb: list, Rb: list, psi_flat) -> np.ndarray:
+    """Y = sum over tasks of c_k (L_t psi[src]) R_t^T, FP64, blocks row-major, flat."""
+    P = _blocks(psi_flat, st)
+    Y = [np.zeros((int(st.m[q]), int(st.n[q]))) for q in range(st.nsec)]
+    for t, (k, s, d) in enumerate(st.tasks):
+        Y[d] += st.term_coef[k] * ((Lb[t] @ P[s]) @ Rb[t].T)
+    return _flat(Y)
+
+
+def heff_dense(st, Lb: list, Rb: list) -> np.ndarray:
+    """Dense H_eff with H[(d,i,j),(s,a,b)] = sum_k c_k L[i,a] R[j,b] (Kronecker brute force)."""
+    off = st.psi_offsets()
+    N = int(off[-1])
+    H = np.zeros((N, N))
+    for t, (k, s, d) in enumerate(st.tasks):
+        blk = st.term_coef[k] * np.kron(Lb[t], Rb[t])    # rows (i,j), cols (a,b), row-major pairs
+        H[off[d]:off[d + 1], off[s]:off[s + 1]] += blk
+    return H
+
+
+def emulated_groups(st):
+    """Task order used by the two emulated stages: tasks grouped by source, then by target
+    (ascending task index inside each group).  Exact integer accumulation makes the result
+    independent of this order; it only fixes where each block sits in the stacked operands."""
+    by_src = [[] for _ in range(st.nsec)]
+    by_dst = [[] for _ in range(st.nsec)]
+    for t, (k, s, d) in enumerate(st.tasks):
+        by_src[s].append(t)
+        by_dst[d].append(t)
+    return by_src, by_dst
+
+
+def heff_apply_emulated(st, Lb: list, Rb: list, psi_flat, S: int, s: int | None = None) -> np.ndarray:
+    """Two-stage emulated H_eff psi.
+
+    Stage 1 (per source q): T = ozaki([L_t1; L_t2; ...], psi[q]) -> T_t blocks.
+    Stage 2 (per target q'): Y[q'] = ozaki([T_t1 T_t2 ...], [(c R_t1)^T; (c R_t2)^T; ...]),
+    where c R is rounded to FP64 first.  Both are one emulated DGEMM each (shared row
+    exponents of the concatenated rows, shared column exponents of the stacked columns).
+    """
+    P = _blocks(psi_flat, st)
+    by_src, by_dst = emulated_groups(st)
+    T = [None] * st.ntask
+    for q in range(st.nsec):
+        ts = by_src[q]
+        if not ts:
+            continue
+        A1 = np.vstack([Lb[t] for t in ts])
+        C1 = ozaki.ozaki_gemm(A1, P[q], S, s)
+        r = 0
+        for t in ts:
+            h = Lb[t].shape[0]
+            T[t] = C1[r:r + h]
+            r += h
+    Y = []
+    for q in range(st.nsec):
+        ts = by_dst[q]
+        if not ts:
+            Y.append(np.zeros((int(st.m[q]), int(st.n[q]))))
+            continue
+        A2 = np.hstack([T[t] for t in ts])
+        B2 = np.vstack([(st.term_coef[st.tasks[t][0]] * Rb[t]).T for t in ts])
+        Y.append(ozaki.ozaki_gemm(A2, B2, S, s))
+    return _flat(Y)
+
+
+def rel_frobenius(y, yref) -> float:
+    y = np.asarray(y, dtype=np.float64)
+    yref = np.asarray(yref, dtype=np.float64)
+    return float(np.linalg.norm(y - yref) / np.linalg.norm(yref))
