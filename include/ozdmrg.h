@@ -1,0 +1,149 @@
+/*
+ * ozdmrg.h -- C ABI of libozdmrg: Ozaki-scheme emulated FP64 products and the block-sparse
+ * two-site effective-Hamiltonian product of ab initio DMRG, on sm_103a (GB300).
+ *
+ * Method (arXiv 2510.04795):
+ *   - section "Theory of emulated FP64 arithmetic": C = A B by (1) fixed point with one exponent
+ *     shared per row of A and per column of B, (2) S slices of 8 bits, (3) all kept slice-pair
+ *     products in low precision, (4) accumulation at high precision and conversion back to FP64;
+ *     products in the less significant ("lower-triangular") part of the S x S grid are skipped;
+ *   - section "Numerical procedure": S slices hold 8S-1 mantissa bits plus the sign
+ *     (S = ceildiv(bits+1, 8));
+ *   - section "Theory of TNS/DMRG regarding error analysis": the DMRG update diagonalises the
+ *     effective Hamiltonian with a Krylov solver, whose matrix-vector product is built from binary
+ *     tensor contractions done as matrix multiplications.
+ *
+ * Conventions for every entry point:
+ *   - matrices are row-major FP64 unless stated; `ld*` is the row stride in elements;
+ *   - pointers named d_* are DEVICE pointers owned by the caller; the library never frees them;
+ *   - work is enqueued on the given CUDA stream and returns before it completes (asynchronous);
+ *     device-side faults of the inputs (NaN/Inf, timeouts of bounded waits) are latched in the
+ *     context and reported by oz_status(), which synchronises the stream;
+ *   - every call returns an int status (OZ_OK or one of the codes below); oz_last_error() gives a
+ *     thread-local message for the last failing call.  No C++ exception crosses the ABI.
+ *
+ * Numerics of the emulation (readings where the paper is silent):
+ *   e_i  = smallest integer with max_k |a_ik| <= (127/128) 2^e_i  (0 for an all-zero row);
+ *   X_ik = RN_even(a_ik 2^(8S-1-e_i)), an integer; slices d_1..d_S = its balanced base-256 digits,
+ *          each in [-128, 127] (INT8), X = sum_t d_t 256^(S-t);
+ *   level s <= S uses d_1..d_s and the pairs t + u <= s + 1 (s(s+1)/2 products);
+ *   C_ij = RN_even(2^(e_i+e_j-2(8S-1)) * sum_{t+u<=s+1} 256^(2S-t-u) P_tu[i][j]) -- the exact
+ *          integer sum rounded ONCE, so the result is bit-identical to the exact definition and
+ *          independent of tiling and summation order.
+ */
+#ifndef OZDMRG_H
+#define OZDMRG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define OZ_OK 0
+#define OZ_EINVAL 1        /* an argument is out of range (message in oz_last_error) */
+#define OZ_ENONFINITE 2    /* an input held NaN or Inf: outputs are unspecified */
+#define OZ_ENOCONV 3       /* an iterative solver reached its iteration limit */
+#define OZ_EVARIATIONAL 4  /* an energy fell below the previous one by more than the tolerance */
+#define OZ_ETIMEOUT 5      /* a bounded device-side wait gave up; outputs are unspecified */
+#define OZ_ECUDA 6         /* a CUDA runtime or library call failed */
+#define OZ_ENOMEM 7        /* device memory could not be allocated */
+
+/* precision / dispatch of a product */
+#define OZ_MODE_EAGER 0    /* every product emulated (the paper's eager mode) */
+#define OZ_MODE_NATIVE 1   /* native FP64 (cuBLAS DGEMM, emulation off) on the same task list */
+
+typedef struct oz_prec {
+  int slices; /* S: digits stored per value, 1..9 */
+  int level;  /* s: digits used, 1..min(S, 8); 0 means s = S */
+  int mode;   /* OZ_MODE_EAGER or OZ_MODE_NATIVE */
+} oz_prec;
+
+typedef void* oz_stream_t; /* a cudaStream_t (0 = legacy default stream) */
+
+typedef struct oz_ctx_s oz_ctx;
+typedef struct oz_heff_s oz_heff;
+
+/* ------------------------------------------------------------------------------------------
+ * Context: one per device.  Owns a grow-only device workspace for ozaki_gemm and the
+ * device-side error latch.  oz_ctx_create makes `device` current on the calling thread.
+ * ------------------------------------------------------------------------------------------ */
+int oz_ctx_create(oz_ctx** out, int device);
+int oz_ctx_destroy(oz_ctx* ctx);
+const char* oz_last_error(void);
+/* Synchronises `stream` and returns (then clears) the latched device status:
+ * OZ_ENONFINITE if a sliced input held NaN/Inf, OZ_ETIMEOUT if a bounded wait gave up. */
+int oz_status(oz_ctx* ctx, oz_stream_t stream);
+
+/* ------------------------------------------------------------------------------------------
+ * ozaki_gemm: C = alpha * (A B) + beta * C with the emulated product of the header comment
+ * (paper, section "Theory of emulated FP64 arithmetic").
+ *   A: m x k (lda >= k), B: k x n (ldb >= n), C: m x n (ldc >= n); all device, row-major.
+ *   alpha*c and beta*C are each rounded to FP64 and then added (no fused multiply-add).
+ *   prec->mode == OZ_MODE_NATIVE runs cuBLAS DGEMM instead.
+ * Errors: OZ_EINVAL for negative sizes, short leading dimensions, slices outside 1..9 or a level
+ * outside 1..min(S,8).  May grow the context workspace (cudaMalloc, synchronous): call it once
+ * outside stream capture before capturing.
+ * ------------------------------------------------------------------------------------------ */
+int ozaki_gemm(oz_ctx* ctx, int m, int n, int k, double alpha, const double* d_A, int lda, const double* d_B,
+               int ldb, double beta, double* d_C, int ldc, const oz_prec* prec, oz_stream_t stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Verification entry points for the slicing and the slice products (same kernels as ozaki_gemm).
+ * ozaki_slice: shared exponents (d_exps[rows]) and digits (d_digits[t][i][j], S x rows x cols,
+ *   int8, t = 0 is the most significant) of the rows of A (rows x cols, lda).
+ * ozaki_slice_products: every slice product P_tu = A^t B^u (A sliced by rows, B by columns):
+ *   d_P[(t*S+u)*m*n + i*n + j] = sum_k dA_t[i][k] dB_u[k][j] as an exact integer in FP64,
+ *   for all t, u < S (the full grid), computed by the tcgen05 kernel at level 1.
+ * ------------------------------------------------------------------------------------------ */
+int ozaki_slice(oz_ctx* ctx, int rows, int cols, const double* d_A, int lda, int slices, int8_t* d_digits,
+                int* d_exps, oz_stream_t stream);
+int ozaki_slice_products(oz_ctx* ctx, int m, int n, int k, const double* d_A, int lda, const double* d_B, int ldb,
+                         int slices, double* d_P, oz_stream_t stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Block-sparse two-site H_eff (paper, section "Theory of TNS/DMRG ...": the Krylov update of the
+ * two-site tensor and binary contractions as matrix products).
+ *
+ * psi is stored as sector blocks q = 0..nsec-1, block q of shape m[q] x n[q] (left enlarged
+ * sector x complementary right sector), row-major, concatenated in q order (offset of block q =
+ * sum_{p<q} m[p] n[p]).  A task adds  coef * L (m[dst] x m[src]) psi[src] R^T  to Y[dst], with
+ * R of shape n[dst] x n[src]; L and R are row-major device blocks owned by the caller.
+ *
+ * heff_apply computes, for every source sector, one emulated product of the stacked L blocks with
+ * psi[src] (the intermediate T, rounded once per element), and for every target sector one
+ * emulated product of the concatenated T blocks with the stacked (coef R)^T blocks.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct oz_task {
+  int src, dst;
+  double coef;
+  const double* d_L; /* m[dst] x m[src] */
+  const double* d_R; /* n[dst] x n[src] */
+} oz_task;
+
+/* Builds the handle: slices every L and coef*R once (they may be freed afterwards in EAGER mode;
+ * NATIVE mode keeps stacked FP64 copies), allocates scratch, tables and a CUDA graph.
+ * Synchronous.  Errors: OZ_EINVAL (sector index out of range, non-positive dims), OZ_ENOMEM,
+ * OZ_ENONFINITE (an operator block held NaN/Inf). */
+int oz_heff_create(oz_ctx* ctx, int nsec, const int* m, const int* n, int ntask, const oz_task* tasks,
+                   const oz_prec* prec, oz_heff** out);
+int oz_heff_destroy(oz_heff* h);
+/* d_y = H_eff d_psi (flat block vectors of length sum m[q] n[q]; d_y must not alias d_psi). */
+int heff_apply(oz_heff* h, const double* d_psi, double* d_y, oz_stream_t stream);
+/* Sizes and bookkeeping of the handle. */
+typedef struct oz_heff_info {
+  long long dim;          /* length of psi */
+  long long flops;        /* FP64 flops of one native product: sum over tasks of 2(m'mn + m'nn') */
+  long long carrier_flops;/* tensor-core flops of one emulated product (padded tiles included) */
+  long long bytes_ops;    /* device bytes held for the operators */
+  long long bytes_scratch;/* device bytes of per-product scratch */
+  long long gemm1_tiles, gemm2_tiles;
+  int slices, level, mode;
+} oz_heff_info;
+int oz_heff_info_get(const oz_heff* h, oz_heff_info* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OZDMRG_H */

@@ -1,0 +1,161 @@
+"""GB300-native Ozaki-scheme emulated FP64 for the two-site DMRG effective-Hamiltonian product.
+
+Thin Python binding over the C ABI of libozdmrg (include/ozdmrg.h); torch supplies device
+memory and streams only.  Names follow the C ABI: ``ozaki_gemm``, ``ozaki_slice``,
+``ozaki_slice_products``, ``heff_apply`` (on an ``Heff`` handle), ``davidson_step``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _native as N
+from ._native import OzError, OZ_MODE_EAGER, OZ_MODE_NATIVE
+
+__all__ = ["Context", "Heff", "OzError", "ozaki_gemm", "ozaki_slice", "ozaki_slice_products", "heff_apply",
+           "OZ_MODE_EAGER", "OZ_MODE_NATIVE"]
+
+
+def _ptr(t: torch.Tensor) -> int:
+    return t.data_ptr()
+
+
+def _stream(stream) -> C.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _prec(slices: int, level: int, mode) -> N.oz_prec:
+    m = {"eager": OZ_MODE_EAGER, "native": OZ_MODE_NATIVE}.get(mode, mode)
+    return N.oz_prec(int(slices), int(level), int(m))
+
+
+def _check_f64(*ts):
+    for t in ts:
+        if t.dtype != torch.float64 or not t.is_cuda:
+            raise OzError(N.OZ_EINVAL, "expected a CUDA float64 tensor")
+
+
+class Context:
+    """One libozdmrg context (device workspace + error latch) on a CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = N.load()
+        self.device = device
+        h = C.c_void_p()
+        N.check(self.lib.oz_ctx_create(C.byref(h), device))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.oz_ctx_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def status(self, stream=None):
+        """Synchronise and raise OzError if a device-side fault was latched."""
+        N.check(self.lib.oz_status(self.h, _stream(stream)))
+
+
+def ozaki_gemm(ctx: Context, A: torch.Tensor, B: torch.Tensor, C_out: torch.Tensor | None = None, alpha=1.0,
+               beta=0.0, slices=7, level=0, mode="eager", stream=None) -> torch.Tensor:
+    """C = alpha * (A B) + beta * C, emulated FP64 (row-major CUDA float64 tensors)."""
+    _check_f64(A, B)
+    m, k = A.shape
+    k2, n = B.shape
+    if k != k2:
+        raise OzError(N.OZ_EINVAL, "inner dimensions differ")
+    if A.stride(1) != 1 or B.stride(1) != 1:
+        raise OzError(N.OZ_EINVAL, "A and B need unit column stride")
+    if C_out is None:
+        C_out = torch.zeros(m, n, dtype=torch.float64, device=A.device)
+    _check_f64(C_out)
+    p = _prec(slices, level, mode)
+    N.check(ctx.lib.ozaki_gemm(ctx.h, m, n, k, float(alpha), _ptr(A), max(A.stride(0), 1), _ptr(B),
+                               max(B.stride(0), 1), float(beta), _ptr(C_out), max(C_out.stride(0), 1),
+                               C.byref(p), _stream(stream)))
+    return C_out
+
+
+def ozaki_slice(ctx: Context, A: torch.Tensor, slices: int, stream=None):
+    """(digits int8 [S, rows, cols], exponents int32 [rows]) of the rows of A."""
+    _check_f64(A)
+    rows, cols = A.shape
+    dig = torch.empty(slices, rows, cols, dtype=torch.int8, device=A.device)
+    ex = torch.empty(rows, dtype=torch.int32, device=A.device)
+    N.check(ctx.lib.ozaki_slice(ctx.h, rows, cols, _ptr(A), A.stride(0), slices, _ptr(dig), _ptr(ex),
+                                _stream(stream)))
+    return dig, ex
+
+
+def ozaki_slice_products(ctx: Context, A: torch.Tensor, B: torch.Tensor, slices: int, stream=None):
+    """Every slice product P[t, u] = A^t B^u as exact integers in float64, shape [S, S, m, n]."""
+    _check_f64(A, B)
+    m, k = A.shape
+    n = B.shape[1]
+    P = torch.empty(slices, slices, m, n, dtype=torch.float64, device=A.device)
+    N.check(ctx.lib.ozaki_slice_products(ctx.h, m, n, k, _ptr(A), A.stride(0), _ptr(B), B.stride(0), slices,
+                                         _ptr(P), _stream(stream)))
+    return P
+
+
+class Heff:
+    """Block-sparse two-site H_eff handle: Y = sum over tasks of coef * L psi[src] R^T into Y[dst].
+
+    ``tasks`` is a sequence of (src, dst, coef, L, R) with L (m[dst] x m[src]) and
+    R (n[dst] x n[src]) CUDA float64 tensors (kept alive by the handle in native mode).
+    """
+
+    def __init__(self, ctx: Context, m, n, tasks, slices=7, level=0, mode="eager"):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        self.m = [int(x) for x in m]
+        self.n = [int(x) for x in n]
+        nsec = len(self.m)
+        arr = (N.oz_task * max(1, len(tasks)))()
+        for i, (s, d, c, L, R) in enumerate(tasks):
+            _check_f64(L, R)
+            if not (L.is_contiguous() and R.is_contiguous()):
+                raise OzError(N.OZ_EINVAL, "task blocks must be contiguous")
+            arr[i] = N.oz_task(int(s), int(d), float(c), _ptr(L), _ptr(R))
+        mm = (C.c_int * nsec)(*self.m)
+        nn = (C.c_int * nsec)(*self.n)
+        p = _prec(slices, level, mode)
+        h = C.c_void_p()
+        N.check(self.lib.oz_heff_create(ctx.h, nsec, mm, nn, len(tasks), arr, C.byref(p), C.byref(h)))
+        self.h = h
+        self.dim = sum(a * b for a, b in zip(self.m, self.n))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.oz_heff_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        inf = N.oz_heff_info()
+        N.check(self.lib.oz_heff_info_get(self.h, C.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in N.oz_heff_info._fields_}
+
+    def apply(self, psi: torch.Tensor, y: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        _check_f64(psi)
+        if y is None:
+            y = torch.empty_like(psi)
+        N.check(self.lib.heff_apply(self.h, _ptr(psi), _ptr(y), _stream(stream)))
+        return y
+
+
+def heff_apply(h: Heff, psi: torch.Tensor, y: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    return h.apply(psi, y, stream)

@@ -1,0 +1,92 @@
+"""ctypes binding of libozdmrg (argument marshalling only; every step runs in the library).
+
+The library is loaded from the package's _lib/ directory.  There is no fallback: a missing or
+unloadable library raises, and calls that fail raise OzError with the library's message.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_LIBPATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libozdmrg.so")
+
+OZ_OK, OZ_EINVAL, OZ_ENONFINITE, OZ_ENOCONV, OZ_EVARIATIONAL, OZ_ETIMEOUT, OZ_ECUDA, OZ_ENOMEM = range(8)
+OZ_MODE_EAGER, OZ_MODE_NATIVE = 0, 1
+STATUS_NAMES = {0: "OZ_OK", 1: "OZ_EINVAL", 2: "OZ_ENONFINITE", 3: "OZ_ENOCONV", 4: "OZ_EVARIATIONAL",
+                5: "OZ_ETIMEOUT", 6: "OZ_ECUDA", 7: "OZ_ENOMEM"}
+
+
+class OzError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class oz_prec(C.Structure):
+    _fields_ = [("slices", C.c_int), ("level", C.c_int), ("mode", C.c_int)]
+
+
+class oz_task(C.Structure):
+    _fields_ = [("src", C.c_int), ("dst", C.c_int), ("coef", C.c_double), ("d_L", C.c_void_p), ("d_R", C.c_void_p)]
+
+
+class oz_heff_info(C.Structure):
+    _fields_ = [("dim", C.c_longlong), ("flops", C.c_longlong), ("carrier_flops", C.c_longlong),
+                ("bytes_ops", C.c_longlong), ("bytes_scratch", C.c_longlong), ("gemm1_tiles", C.c_longlong),
+                ("gemm2_tiles", C.c_longlong), ("slices", C.c_int), ("level", C.c_int), ("mode", C.c_int)]
+
+
+class oz_davidson_opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("max_sub", C.c_int)]
+
+
+class oz_davidson_result(C.Structure):
+    _fields_ = [("theta", C.c_double), ("resid", C.c_double), ("iters", C.c_int), ("converged", C.c_int)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _LIBPATH
+
+
+def load():
+    """Load (once) and declare the C ABI.  Raises if the library is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIBPATH):
+        raise OzError(OZ_ECUDA, f"libozdmrg.so not built ({_LIBPATH}); run __graft_entry__.build()")
+    L = C.CDLL(_LIBPATH)
+    vp, i, d, ll = C.c_void_p, C.c_int, C.c_double, C.c_longlong
+    sig = {
+        "oz_ctx_create": (i, [C.POINTER(vp), i]),
+        "oz_ctx_destroy": (i, [vp]),
+        "oz_last_error": (C.c_char_p, []),
+        "oz_status": (i, [vp, vp]),
+        "ozaki_gemm": (i, [vp, i, i, i, d, vp, i, vp, i, d, vp, i, C.POINTER(oz_prec), vp]),
+        "ozaki_slice": (i, [vp, i, i, vp, i, i, vp, vp, vp]),
+        "ozaki_slice_products": (i, [vp, i, i, i, vp, i, vp, i, i, vp, vp]),
+        "oz_heff_create": (i, [vp, i, C.POINTER(i), C.POINTER(i), i, C.POINTER(oz_task), C.POINTER(oz_prec),
+                               C.POINTER(vp)]),
+        "oz_heff_destroy": (i, [vp]),
+        "heff_apply": (i, [vp, vp, vp, vp]),
+        "oz_heff_info_get": (i, [vp, C.POINTER(oz_heff_info)]),
+        "oz_heff_diag": (i, [vp, vp, vp]),
+        "davidson_step": (i, [vp, vp, vp, C.POINTER(oz_davidson_result), vp]),
+        "davidson_solve": (i, [vp, vp, C.POINTER(oz_davidson_opts), C.POINTER(oz_davidson_result), vp]),
+    }
+    for name, (res, args) in sig.items():
+        if not hasattr(L, name):
+            continue
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def check(rc: int):
+    if rc != OZ_OK:
+        raise OzError(rc, load().oz_last_error().decode(errors="replace"))

@@ -1,0 +1,767 @@
+// C ABI of libozdmrg: contexts, ozaki_gemm, verification entries and the H_eff handle.
+// Host orchestration only; every step of a product runs in the kernels of oz_slice.cu and
+// oz_gemm.cu (or cuBLAS DGEMM in OZ_MODE_NATIVE).
+#include <cublas_v2.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ozdmrg.h"
+#include "oz_gemm.cuh"
+#include "oz_slice.cuh"
+
+using oz::GemmProblem;
+using oz::GemmTile;
+using oz::SliceSeg;
+
+namespace {
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(e == cudaErrorMemoryAllocation ? OZ_ENOMEM : OZ_ECUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define OZ_CU(call)                                   \
+  do {                                                \
+    cudaError_t _e = (call);                          \
+    if (_e != cudaSuccess) return cuda_fail(_e, #call); \
+  } while (0)
+
+inline long long cdiv(long long a, long long b) { return (a + b - 1) / b; }
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int check_prec(const oz_prec* p, int* S, int* s, int* mode) {
+  if (!p) return fail(OZ_EINVAL, "prec is null");
+  if (p->slices < 1 || p->slices > 9) return fail(OZ_EINVAL, "slices must be in 1..9");
+  int lvl = p->level == 0 ? p->slices : p->level;
+  if (lvl < 1 || lvl > p->slices || lvl > oz::MAX_LEVEL) return fail(OZ_EINVAL, "level must be in 1..min(S,8)");
+  if (p->mode != OZ_MODE_EAGER && p->mode != OZ_MODE_NATIVE) return fail(OZ_EINVAL, "unknown mode");
+  *S = p->slices;
+  *s = lvl;
+  *mode = p->mode;
+  return OZ_OK;
+}
+
+__global__ void scale_kernel(double* C, int m, int n, int ldc, double beta) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)m * n) return;
+  int i = (int)(idx / n), j = (int)(idx % n);
+  double* c = C + (long long)i * ldc + j;
+  *c = beta == 0.0 ? 0.0 : __dmul_rn(beta, *c);
+}
+__global__ void fill_int_kernel(int* p, long long n, int v) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < n) p[idx] = v;
+}
+}  // namespace
+
+struct oz_ctx_s {
+  int device = 0;
+  int nsm = 0;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  int* d_flags = nullptr;  // [0] non-finite input, [1] kernel timeout/abort
+  cublasHandle_t cublas = nullptr;
+
+  // bump allocation inside the workspace (grown with cudaMalloc when too small)
+  int reserve(size_t bytes) {
+    if (bytes <= ws_bytes) return OZ_OK;
+    if (ws) {
+      cudaDeviceSynchronize();
+      cudaFree(ws);
+      ws = nullptr;
+      ws_bytes = 0;
+    }
+    size_t b = std::max(bytes, (size_t)64 << 20);
+    cudaError_t e = cudaMalloc(&ws, b);
+    if (e != cudaSuccess) return cuda_fail(e, "workspace cudaMalloc");
+    ws_bytes = b;
+    return OZ_OK;
+  }
+};
+
+extern "C" const char* oz_last_error(void) { return g_err.c_str(); }
+
+extern "C" int oz_ctx_create(oz_ctx** out, int device) {
+  if (!out) return fail(OZ_EINVAL, "out is null");
+  *out = nullptr;
+  OZ_CU(cudaSetDevice(device));
+  cudaDeviceProp prop;
+  OZ_CU(cudaGetDeviceProperties(&prop, device));
+  if (prop.major != 10 || prop.minor != 3)
+    return fail(OZ_EINVAL, "libozdmrg is built for sm_103a (GB300); found sm_" + std::to_string(prop.major) +
+                               std::to_string(prop.minor));
+  oz_ctx* c = new oz_ctx_s();
+  c->device = device;
+  c->nsm = prop.multiProcessorCount;
+  cudaError_t e = cudaMalloc(&c->d_flags, 16);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "cudaMalloc flags");
+  }
+  cudaMemset(c->d_flags, 0, 16);
+  if (cublasCreate(&c->cublas) != CUBLAS_STATUS_SUCCESS) {
+    cudaFree(c->d_flags);
+    delete c;
+    return fail(OZ_ECUDA, "cublasCreate failed");
+  }
+  // native FP64 comparator: default math (no fixed-point emulation)
+  cublasSetMathMode(c->cublas, CUBLAS_DEFAULT_MATH);
+  *out = c;
+  return OZ_OK;
+}
+
+extern "C" int oz_ctx_destroy(oz_ctx* c) {
+  if (!c) return OZ_OK;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  if (c->cublas) cublasDestroy(c->cublas);
+  if (c->ws) cudaFree(c->ws);
+  if (c->d_flags) cudaFree(c->d_flags);
+  delete c;
+  return OZ_OK;
+}
+
+extern "C" int oz_status(oz_ctx* c, oz_stream_t stream) {
+  if (!c) return fail(OZ_EINVAL, "ctx is null");
+  OZ_CU(cudaStreamSynchronize((cudaStream_t)stream));
+  int f[4];
+  OZ_CU(cudaMemcpy(f, c->d_flags, 16, cudaMemcpyDeviceToHost));
+  OZ_CU(cudaMemset(c->d_flags, 0, 16));
+  if (f[1]) return fail(OZ_ETIMEOUT, "a bounded device wait gave up (kernel aborted)");
+  if (f[0]) return fail(OZ_ENONFINITE, "an input held NaN or Inf");
+  return OZ_OK;
+}
+
+// --------------------------------------------------------------------------------------------
+// dense products
+// --------------------------------------------------------------------------------------------
+namespace {
+struct DenseOperands {
+  __half* dA;
+  __half* dB;
+  unsigned long long* mx;
+  int* ex;
+  int nkb, nrbA, nrbB, mpad, npad;
+};
+
+// Workspace layout and slicing of A (rows) and B (columns) for one product.
+int slice_pair(oz_ctx* c, int m, int n, int k, const double* A, int lda, const double* B, int ldb, int S,
+               DenseOperands& o, cudaStream_t st) {
+  o.nkb = (int)cdiv(k, oz::KB);
+  o.nrbA = (int)cdiv(m, oz::TILE_M);
+  o.nrbB = (int)cdiv(n, oz::BN);
+  o.mpad = o.nrbA * oz::TILE_M;
+  o.npad = o.nrbB * oz::BN;
+  size_t bA = (size_t)o.nrbA * o.nkb * S * oz::TILE_M * oz::KB * 2;
+  size_t bB = (size_t)o.nrbB * o.nkb * S * oz::BN * oz::KB * 2;
+  size_t bM = (size_t)(o.mpad + o.npad) * 8;
+  size_t bE = (size_t)(o.mpad + o.npad) * 4;
+  size_t need = align256(bA) + align256(bB) + align256(bM) + align256(bE) + 256;
+  int rc = c->reserve(need);
+  if (rc) return rc;
+  char* p = c->ws;
+  o.dA = (__half*)p;
+  p += align256(bA);
+  o.dB = (__half*)p;
+  p += align256(bB);
+  o.mx = (unsigned long long*)p;
+  p += align256(bM);
+  o.ex = (int*)p;
+  OZ_CU(cudaMemsetAsync(o.mx, 0, bM, st));
+  oz::SegPack pk{};
+  SliceSeg& a = pk.seg[0];
+  a.src = A; a.ld = lda; a.rows = m; a.cols = k; a.prows = o.mpad; a.pcols = o.nkb * oz::KB;
+  a.r0 = 0; a.k0 = 0; a.trans = 0; a.S = S; a.scale = 1.0; a.dst = o.dA; a.TR = oz::TILE_M; a.nkb = o.nkb;
+  a.rowmax = o.mx; a.rowexp = o.ex; a.unit0 = 0; a.unit0m = 0;
+  SliceSeg& b = pk.seg[1];
+  b.src = B; b.ld = ldb; b.rows = n; b.cols = k; b.prows = o.npad; b.pcols = o.nkb * oz::KB;
+  b.r0 = 0; b.k0 = 0; b.trans = 1; b.S = S; b.scale = 1.0; b.dst = o.dB; b.TR = oz::BN; b.nkb = o.nkb;
+  b.rowmax = o.mx + o.mpad; b.rowexp = o.ex + o.mpad;
+  b.unit0 = oz::digit_units(a.prows, a.pcols);
+  b.unit0m = oz::rowmax_units(a.rows, a.cols);
+  const int nseg = B ? 2 : 1;
+  long long um = b.unit0m + (B ? oz::rowmax_units(b.rows, b.cols) : 0);
+  long long ud = b.unit0 + (B ? oz::digit_units(b.prows, b.pcols) : 0);
+  OZ_CU(oz::launch_rowmax(nullptr, &pk, nseg, um, c->d_flags, st));
+  OZ_CU(oz::launch_digits(nullptr, &pk, nseg, ud, S, st));
+  return OZ_OK;
+}
+}  // namespace
+
+extern "C" int ozaki_gemm(oz_ctx* c, int m, int n, int k, double alpha, const double* A, int lda, const double* B,
+                          int ldb, double beta, double* C, int ldc, const oz_prec* prec, oz_stream_t stream) {
+  if (!c) return fail(OZ_EINVAL, "ctx is null");
+  int S, s, mode;
+  if (int rc = check_prec(prec, &S, &s, &mode)) return rc;
+  if (m < 0 || n < 0 || k < 0) return fail(OZ_EINVAL, "negative size");
+  if (lda < std::max(k, 1) || ldb < std::max(n, 1) || ldc < std::max(n, 1)) return fail(OZ_EINVAL, "leading dimension too small");
+  if (m == 0 || n == 0) return OZ_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (k == 0) {
+    scale_kernel<<<(unsigned)cdiv((long long)m * n, 256), 256, 0, st>>>(C, m, n, ldc, beta);
+    OZ_CU(cudaGetLastError());
+    return OZ_OK;
+  }
+  if (mode == OZ_MODE_NATIVE) {
+    cublasSetStream(c->cublas, st);
+    // row-major C = A B  <=>  column-major C^T = B^T A^T
+    if (cublasDgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_N, n, m, k, &alpha, B, ldb, A, lda, &beta, C, ldc) !=
+        CUBLAS_STATUS_SUCCESS)
+      return fail(OZ_ECUDA, "cublasDgemm failed");
+    return OZ_OK;
+  }
+  DenseOperands o;
+  if (int rc = slice_pair(c, m, n, k, A, lda, B, ldb, S, o, st)) return rc;
+  GemmProblem P{};
+  P.A = o.dA; P.B = o.dB; P.ea = o.ex; P.eb = o.ex + o.mpad;
+  P.M = m; P.N = n; P.nkb = o.nkb; P.SA = S; P.SB = S; P.s = s;
+  P.mode = oz::OUT_DENSE; P.C = C; P.ldc = ldc; P.alpha = alpha; P.beta = beta;
+  int ntiles = o.nrbA * o.nrbB;
+  OZ_CU(oz::launch_gemm(nullptr, nullptr, ntiles, c->nsm, &P, c->d_flags + 1, st));
+  return OZ_OK;
+}
+
+extern "C" int ozaki_slice(oz_ctx* c, int rows, int cols, const double* A, int lda, int slices, int8_t* digits,
+                           int* exps, oz_stream_t stream) {
+  if (!c) return fail(OZ_EINVAL, "ctx is null");
+  if (rows <= 0 || cols <= 0 || lda < cols) return fail(OZ_EINVAL, "bad sizes");
+  if (slices < 1 || slices > 9) return fail(OZ_EINVAL, "slices must be in 1..9");
+  cudaStream_t st = (cudaStream_t)stream;
+  DenseOperands o;
+  if (int rc = slice_pair(c, rows, 1, cols, A, lda, nullptr, 1, slices, o, st)) return rc;
+  OZ_CU(oz::launch_untile(o.dA, oz::TILE_M, o.nkb, slices, rows, cols, digits, st));
+  OZ_CU(cudaMemcpyAsync(exps, o.ex, (size_t)rows * 4, cudaMemcpyDeviceToDevice, st));
+  return OZ_OK;
+}
+
+extern "C" int ozaki_slice_products(oz_ctx* c, int m, int n, int k, const double* A, int lda, const double* B,
+                                    int ldb, int slices, double* Pout, oz_stream_t stream) {
+  if (!c) return fail(OZ_EINVAL, "ctx is null");
+  if (m <= 0 || n <= 0 || k <= 0 || lda < k || ldb < n) return fail(OZ_EINVAL, "bad sizes");
+  if (slices < 1 || slices > 9) return fail(OZ_EINVAL, "slices must be in 1..9");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int S = slices;
+  DenseOperands o;
+  if (int rc = slice_pair(c, m, n, k, A, lda, B, ldb, S, o, st)) return rc;
+  // unit exponents (7 + 7 - 8 - 6 = 0): the epilogue then returns the integer P_tu itself
+  int* sevens = nullptr;
+  {
+    size_t used = (size_t)((char*)(o.ex + o.mpad + o.npad) - c->ws);
+    size_t need = align256(used) + align256((size_t)std::max(o.mpad, o.npad) * 4);
+    if (need > c->ws_bytes) return fail(OZ_ENOMEM, "workspace too small for slice products");
+    sevens = (int*)(c->ws + align256(used));
+    long long ne = std::max(o.mpad, o.npad);
+    fill_int_kernel<<<(unsigned)cdiv(ne, 256), 256, 0, st>>>(sevens, ne, 7);
+    OZ_CU(cudaGetLastError());
+  }
+  for (int t = 0; t < S; ++t)
+    for (int u = 0; u < S; ++u) {
+      GemmProblem P{};
+      P.A = o.dA + (size_t)t * oz::TILE_M * oz::KB;
+      P.B = o.dB + (size_t)u * oz::BN * oz::KB;
+      P.ea = sevens; P.eb = sevens;
+      P.M = m; P.N = n; P.nkb = o.nkb; P.SA = S; P.SB = S; P.s = 1;
+      P.mode = oz::OUT_DENSE; P.C = Pout + (size_t)(t * S + u) * m * n; P.ldc = n; P.alpha = 1.0; P.beta = 0.0;
+      OZ_CU(oz::launch_gemm(nullptr, nullptr, o.nrbA * o.nrbB, c->nsm, &P, c->d_flags + 1, st));
+    }
+  return OZ_OK;
+}
+
+// --------------------------------------------------------------------------------------------
+// H_eff handle
+// --------------------------------------------------------------------------------------------
+struct oz_heff_s {
+  oz_ctx* ctx = nullptr;
+  int nsec = 0, ntask = 0, S = 7, s = 7, mode = OZ_MODE_EAGER;
+  std::vector<int> m, n;
+  std::vector<long long> psioff;
+  long long dim = 0, flops = 0, carrier_flops = 0, bytes_ops = 0, bytes_scratch = 0;
+  std::vector<void*> allocs;
+
+  // emulated path
+  __half *dA1 = nullptr, *dB1 = nullptr, *dA2 = nullptr, *dB2 = nullptr;
+  double* dStage = nullptr;
+  int *eB1 = nullptr, *eA2 = nullptr;
+  unsigned long long *mB1 = nullptr, *mA2 = nullptr;
+  size_t bytes_mB1 = 0, bytes_mA2 = 0;
+  GemmProblem *dP1 = nullptr, *dP2 = nullptr;
+  GemmTile *dT1 = nullptr, *dT2 = nullptr;
+  int nt1 = 0, nt2 = 0;
+  SliceSeg *dSegPsi = nullptr, *dSegA2 = nullptr;
+  int nsegPsi = 0, nsegA2 = 0;
+  long long uPsiM = 0, uPsiD = 0, uA2D = 0;
+  bool zero_y = false;
+
+  // native path (stacked FP64 copies)
+  double *nA1 = nullptr, *nB2 = nullptr, *nT = nullptr;
+  struct NatG1 { long long a1off, toff; int rows, kdim, q; };
+  struct NatG2 { long long stoff, b2off; int q, ld2; };
+  std::vector<NatG1> nat1;
+  std::vector<NatG2> nat2;
+  long long* dScatter = nullptr;  // per stacked T row: destination offset in the staging buffer
+  long long nTrows = 0;
+
+  double *dPsi = nullptr, *dY = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+
+  template <class T>
+  int alloc(T** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 256;
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    allocs.push_back((void*)*p);
+    return OZ_OK;
+  }
+  int enqueue(cudaStream_t st);
+};
+
+namespace {
+__global__ void scatter_rows_kernel(const double* __restrict__ T, const long long* __restrict__ rowinfo,
+                                    double* __restrict__ stage) {
+  // one block per row: rowinfo[2r] = source offset in T, rowinfo[2r+1] = destination offset | (ncols << 40)
+  long long r = blockIdx.x;
+  long long src = rowinfo[2 * r], d = rowinfo[2 * r + 1];
+  int nc = (int)(d >> 40);
+  long long dst = d & ((1ll << 40) - 1);
+  for (int j = threadIdx.x; j < nc; j += blockDim.x) stage[dst + j] = T[src + j];
+}
+}  // namespace
+
+int oz_heff_s::enqueue(cudaStream_t st) {
+  if (mode == OZ_MODE_EAGER) {
+    if (bytes_mB1) OZ_CU(cudaMemsetAsync(mB1, 0, bytes_mB1, st));
+    if (bytes_mA2) OZ_CU(cudaMemsetAsync(mA2, 0, bytes_mA2, st));
+    OZ_CU(oz::launch_rowmax(dSegPsi, nullptr, nsegPsi, uPsiM, ctx->d_flags, st));
+    OZ_CU(oz::launch_digits(dSegPsi, nullptr, nsegPsi, uPsiD, S, st));
+    OZ_CU(oz::launch_gemm(dP1, dT1, nt1, ctx->nsm, nullptr, ctx->d_flags + 1, st));
+    OZ_CU(oz::launch_digits(dSegA2, nullptr, nsegA2, uA2D, S, st));
+    if (zero_y) OZ_CU(cudaMemsetAsync(dY, 0, (size_t)dim * 8, st));
+    OZ_CU(oz::launch_gemm(dP2, dT2, nt2, ctx->nsm, nullptr, ctx->d_flags + 1, st));
+    return OZ_OK;
+  }
+  // native FP64: one DGEMM per source sector, scatter into the concatenated layout, one per target
+  cublasSetStream(ctx->cublas, st);
+  const double one = 1.0, zero = 0.0;
+  for (const auto& g : nat1) {
+    // T (rows x n[q]) = A1 (rows x m[q]) psi[q] (m[q] x n[q]), row-major
+    int nq = n[g.q];
+    if (cublasDgemm(ctx->cublas, CUBLAS_OP_N, CUBLAS_OP_N, nq, g.rows, g.kdim, &one, dPsi + psioff[g.q], nq,
+                    nA1 + g.a1off, g.kdim, &zero, nT + g.toff, nq) != CUBLAS_STATUS_SUCCESS)
+      return fail(OZ_ECUDA, "cublasDgemm (stage 1)");
+  }
+  if (nTrows > 0) {
+    scatter_rows_kernel<<<(unsigned)nTrows, 128, 0, st>>>(nT, dScatter, dStage);
+    OZ_CU(cudaGetLastError());
+  }
+  if (zero_y) OZ_CU(cudaMemsetAsync(dY, 0, (size_t)dim * 8, st));
+  for (const auto& g : nat2) {
+    // Y[q] (m x n') = Stage (m x ld2) B2T^T, B2T: n' x ld2 row-major
+    int mq = m[g.q], nq = n[g.q];
+    if (cublasDgemm(ctx->cublas, CUBLAS_OP_T, CUBLAS_OP_N, nq, mq, g.ld2, &one, nB2 + g.b2off, g.ld2,
+                    dStage + g.stoff, g.ld2, &zero, dY + psioff[g.q], nq) != CUBLAS_STATUS_SUCCESS)
+      return fail(OZ_ECUDA, "cublasDgemm (stage 2)");
+  }
+  return OZ_OK;
+}
+
+namespace {
+__global__ void copy_block_kernel(const double* __restrict__ src, int rows, int cols, long long lds, double scale,
+                                  double* __restrict__ dst, long long ldd) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)rows * cols) return;
+  int i = (int)(idx / cols), j = (int)(idx % cols);
+  double v = src[(long long)i * lds + j];
+  dst[(long long)i * ldd + j] = scale != 1.0 ? __dmul_rn(v, scale) : v;
+}
+}  // namespace
+
+extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, int ntask, const oz_task* tasks,
+                              const oz_prec* prec, oz_heff** out) {
+  if (!out) return fail(OZ_EINVAL, "out is null");
+  *out = nullptr;
+  if (!c) return fail(OZ_EINVAL, "ctx is null");
+  int S, s, mode;
+  if (int rc = check_prec(prec, &S, &s, &mode)) return rc;
+  if (nsec <= 0 || ntask < 0 || !m || !n || (ntask > 0 && !tasks)) return fail(OZ_EINVAL, "bad structure");
+  for (int q = 0; q < nsec; ++q)
+    if (m[q] <= 0 || n[q] <= 0) return fail(OZ_EINVAL, "sector dims must be positive");
+  for (int t = 0; t < ntask; ++t) {
+    if (tasks[t].src < 0 || tasks[t].src >= nsec || tasks[t].dst < 0 || tasks[t].dst >= nsec)
+      return fail(OZ_EINVAL, "task sector out of range");
+    if (!tasks[t].d_L || !tasks[t].d_R) return fail(OZ_EINVAL, "task block pointer is null");
+  }
+  OZ_CU(cudaSetDevice(c->device));
+  oz_heff* h = new oz_heff_s();
+  h->ctx = c;
+  h->nsec = nsec;
+  h->ntask = ntask;
+  h->S = S;
+  h->s = s;
+  h->mode = mode;
+  h->m.assign(m, m + nsec);
+  h->n.assign(n, n + nsec);
+  h->psioff.assign(nsec + 1, 0);
+  for (int q = 0; q < nsec; ++q) h->psioff[q + 1] = h->psioff[q] + (long long)m[q] * n[q];
+  h->dim = h->psioff[nsec];
+  auto bail = [&](int rc) {
+    oz_heff_destroy(h);
+    return rc;
+  };
+
+  std::vector<std::vector<int>> bysrc(nsec), bydst(nsec);
+  for (int t = 0; t < ntask; ++t) {
+    bysrc[tasks[t].src].push_back(t);
+    bydst[tasks[t].dst].push_back(t);
+    const long long mp = m[tasks[t].dst], mm = m[tasks[t].src], nn = n[tasks[t].src], nq = n[tasks[t].dst];
+    h->flops += 2 * (mp * mm * nn + mp * nn * nq);
+  }
+  for (int q = 0; q < nsec; ++q)
+    if (bydst[q].empty()) h->zero_y = true;
+
+  // ---- layout of stage 1 (per source sector) and stage 2 (per target sector)
+  std::vector<int> rows1(nsec, 0), nkb1(nsec), nkb2(nsec), ld2(nsec);
+  std::vector<long long> offk(ntask, 0), rowin1(ntask, 0);
+  for (int q = 0; q < nsec; ++q) {
+    for (int t : bysrc[q]) {
+      rowin1[t] = rows1[q];
+      rows1[q] += m[tasks[t].dst];
+    }
+    nkb1[q] = (int)cdiv(m[q], oz::KB);
+    long long k2 = 0;
+    for (int t : bydst[q]) {
+      offk[t] = k2;
+      k2 += cdiv(n[tasks[t].src], 8) * 8;
+    }
+    nkb2[q] = (int)cdiv(std::max(k2, 1ll), oz::KB);
+    ld2[q] = nkb2[q] * oz::KB;
+  }
+  std::vector<long long> stoff(nsec + 1, 0);
+  for (int q = 0; q < nsec; ++q) stoff[q + 1] = stoff[q] + (long long)m[q] * ld2[q];
+  const long long A1tile = (long long)oz::TILE_M * oz::KB, Btile = (long long)oz::BN * oz::KB;
+  std::vector<long long> A1off(nsec + 1, 0), B1off(nsec + 1, 0), A2off(nsec + 1, 0), B2off(nsec + 1, 0);
+  std::vector<long long> A1row(nsec + 1, 0), B1row(nsec + 1, 0), A2row(nsec + 1, 0), B2row(nsec + 1, 0);
+  for (int q = 0; q < nsec; ++q) {
+    long long nrbA1 = cdiv(rows1[q], oz::TILE_M), nrbB1 = cdiv(n[q], oz::BN);
+    long long nrbA2 = cdiv(m[q], oz::TILE_M), nrbB2 = cdiv(n[q], oz::BN);
+    A1off[q + 1] = A1off[q] + nrbA1 * nkb1[q] * S * A1tile;
+    B1off[q + 1] = B1off[q] + nrbB1 * nkb1[q] * S * Btile;
+    A2off[q + 1] = A2off[q] + nrbA2 * nkb2[q] * S * A1tile;
+    B2off[q + 1] = B2off[q] + nrbB2 * nkb2[q] * S * Btile;
+    A1row[q + 1] = A1row[q] + nrbA1 * oz::TILE_M;
+    B1row[q + 1] = B1row[q] + nrbB1 * oz::BN;
+    A2row[q + 1] = A2row[q] + nrbA2 * oz::TILE_M;
+    B2row[q + 1] = B2row[q] + nrbB2 * oz::BN;
+  }
+  const long long P1 = (long long)s * (s + 1) / 2;
+  for (int q = 0; q < nsec; ++q) {
+    h->carrier_flops += P1 * 2 * (cdiv(rows1[q], oz::TILE_M) * oz::TILE_M) * (cdiv(n[q], oz::BN) * oz::BN) *
+                        ((long long)nkb1[q] * oz::KB);
+    if (!bydst[q].empty())
+      h->carrier_flops += P1 * 2 * (cdiv(m[q], oz::TILE_M) * oz::TILE_M) * (cdiv(n[q], oz::BN) * oz::BN) *
+                          ((long long)nkb2[q] * oz::KB);
+  }
+
+  int rc;
+  if ((rc = h->alloc(&h->dPsi, (size_t)h->dim * 8))) return bail(rc);
+  if ((rc = h->alloc(&h->dY, (size_t)h->dim * 8))) return bail(rc);
+  if ((rc = h->alloc(&h->dStage, (size_t)stoff[nsec] * 8))) return bail(rc);
+  OZ_CU(cudaMemset(h->dStage, 0, (size_t)stoff[nsec] * 8));
+  h->bytes_scratch = (long long)stoff[nsec] * 8 + 2 * h->dim * 8;
+
+  if (mode == OZ_MODE_NATIVE) {
+    // stacked FP64 copies: A1 (per source: rows1 x m[q]) and B2T (per target: n[q] x ld2, zero padded)
+    std::vector<long long> a1o(nsec + 1, 0), b2o(nsec + 1, 0), to(nsec + 1, 0);
+    for (int q = 0; q < nsec; ++q) {
+      a1o[q + 1] = a1o[q] + (long long)rows1[q] * m[q];
+      b2o[q + 1] = b2o[q] + (long long)n[q] * ld2[q];
+      to[q + 1] = to[q] + (long long)rows1[q] * n[q];
+    }
+    if ((rc = h->alloc(&h->nA1, (size_t)a1o[nsec] * 8))) return bail(rc);
+    if ((rc = h->alloc(&h->nB2, (size_t)b2o[nsec] * 8))) return bail(rc);
+    if ((rc = h->alloc(&h->nT, (size_t)to[nsec] * 8))) return bail(rc);
+    OZ_CU(cudaMemset(h->nB2, 0, (size_t)b2o[nsec] * 8));
+    h->bytes_ops = (a1o[nsec] + b2o[nsec]) * 8;
+    h->bytes_scratch += to[nsec] * 8;
+    for (int t = 0; t < ntask; ++t) {
+      const oz_task& tk = tasks[t];
+      int q = tk.src, d = tk.dst;
+      long long rows = m[d], cols = m[q];
+      copy_block_kernel<<<(unsigned)cdiv(rows * cols, 256), 256>>>(tk.d_L, (int)rows, (int)cols, cols, 1.0,
+                                                                  h->nA1 + a1o[q] + rowin1[t] * m[q], m[q]);
+      rows = n[d];
+      cols = n[q];
+      copy_block_kernel<<<(unsigned)cdiv(rows * cols, 256), 256>>>(tk.d_R, (int)rows, (int)cols, cols, tk.coef,
+                                                                  h->nB2 + b2o[d] + offk[t], ld2[d]);
+    }
+    OZ_CU(cudaGetLastError());
+    std::vector<long long> sc;
+    sc.reserve(2 * (size_t)to[nsec]);
+    for (int q = 0; q < nsec; ++q) {
+      if (bysrc[q].empty()) continue;
+      h->nat1.push_back({a1o[q], to[q], rows1[q], m[q], q});
+      for (int t : bysrc[q]) {
+        int d = tasks[t].dst;
+        for (int i = 0; i < m[d]; ++i) {
+          long long srcoff = to[q] + (rowin1[t] + i) * n[q];
+          long long dstoff = stoff[d] + (long long)i * ld2[d] + offk[t];
+          sc.push_back(srcoff);
+          sc.push_back(dstoff | ((long long)n[q] << 40));
+        }
+      }
+    }
+    h->nTrows = (long long)sc.size() / 2;
+    if ((rc = h->alloc(&h->dScatter, sc.size() * 8))) return bail(rc);
+    OZ_CU(cudaMemcpy(h->dScatter, sc.data(), sc.size() * 8, cudaMemcpyHostToDevice));
+    for (int q = 0; q < nsec; ++q)
+      if (!bydst[q].empty()) h->nat2.push_back({stoff[q], b2o[q], q, ld2[q]});
+    OZ_CU(cudaDeviceSynchronize());
+  } else {
+    // ---- device buffers of the emulated path
+    size_t bA1 = A1off[nsec] * 2, bB1 = B1off[nsec] * 2, bA2 = A2off[nsec] * 2, bB2 = B2off[nsec] * 2;
+    if ((rc = h->alloc(&h->dA1, bA1))) return bail(rc);
+    if ((rc = h->alloc(&h->dB1, bB1))) return bail(rc);
+    if ((rc = h->alloc(&h->dA2, bA2))) return bail(rc);
+    if ((rc = h->alloc(&h->dB2, bB2))) return bail(rc);
+    OZ_CU(cudaMemset(h->dA1, 0, bA1));
+    OZ_CU(cudaMemset(h->dB1, 0, bB1));
+    OZ_CU(cudaMemset(h->dA2, 0, bA2));
+    OZ_CU(cudaMemset(h->dB2, 0, bB2));
+    h->bytes_ops = (long long)(bA1 + bB2);
+    h->bytes_scratch += (long long)(bB1 + bA2);
+    int *eA1, *eB2;
+    unsigned long long *mA1, *mB2;
+    if ((rc = h->alloc(&eA1, A1row[nsec] * 4))) return bail(rc);
+    if ((rc = h->alloc(&eB2, B2row[nsec] * 4))) return bail(rc);
+    if ((rc = h->alloc(&h->eB1, B1row[nsec] * 4))) return bail(rc);
+    if ((rc = h->alloc(&h->eA2, A2row[nsec] * 4))) return bail(rc);
+    if ((rc = h->alloc(&mA1, A1row[nsec] * 8))) return bail(rc);
+    if ((rc = h->alloc(&mB2, B2row[nsec] * 8))) return bail(rc);
+    h->bytes_mB1 = B1row[nsec] * 8;
+    h->bytes_mA2 = A2row[nsec] * 8;
+    if ((rc = h->alloc(&h->mB1, h->bytes_mB1))) return bail(rc);
+    if ((rc = h->alloc(&h->mA2, h->bytes_mA2))) return bail(rc);
+    OZ_CU(cudaMemset(mA1, 0, A1row[nsec] * 8));
+    OZ_CU(cudaMemset(mB2, 0, B2row[nsec] * 8));
+
+    // ---- operator slicing (once): L blocks into A1, coef*R blocks into B2T
+    std::vector<SliceSeg> ops;
+    ops.reserve(2 * (size_t)ntask);
+    long long um = 0, ud = 0;
+    for (int q = 0; q < nsec; ++q)
+      for (int t : bysrc[q]) {
+        const oz_task& tk = tasks[t];
+        SliceSeg g{};
+        g.src = tk.d_L; g.ld = m[q]; g.rows = m[tk.dst]; g.cols = m[q]; g.prows = g.rows; g.pcols = g.cols;
+        g.r0 = (int)rowin1[t]; g.k0 = 0; g.trans = 0; g.S = S; g.scale = 1.0;
+        g.dst = h->dA1 + A1off[q]; g.TR = oz::TILE_M; g.nkb = nkb1[q];
+        g.rowmax = mA1 + A1row[q]; g.rowexp = eA1 + A1row[q];
+        g.unit0 = ud; g.unit0m = um;
+        ud += oz::digit_units(g.prows, g.pcols);
+        um += oz::rowmax_units(g.rows, g.cols);
+        ops.push_back(g);
+      }
+    for (int q = 0; q < nsec; ++q)
+      for (int t : bydst[q]) {
+        const oz_task& tk = tasks[t];
+        SliceSeg g{};
+        g.src = tk.d_R; g.ld = n[tk.src]; g.rows = n[q]; g.cols = n[tk.src]; g.prows = g.rows; g.pcols = g.cols;
+        g.r0 = 0; g.k0 = (int)offk[t]; g.trans = 0; g.S = S; g.scale = tk.coef;
+        g.dst = h->dB2 + B2off[q]; g.TR = oz::BN; g.nkb = nkb2[q];
+        g.rowmax = mB2 + B2row[q]; g.rowexp = eB2 + B2row[q];
+        g.unit0 = ud; g.unit0m = um;
+        ud += oz::digit_units(g.prows, g.pcols);
+        um += oz::rowmax_units(g.rows, g.cols);
+        ops.push_back(g);
+      }
+    if (!ops.empty()) {
+      SliceSeg* dops;
+      OZ_CU(cudaMalloc(&dops, ops.size() * sizeof(SliceSeg)));
+      cudaMemcpy(dops, ops.data(), ops.size() * sizeof(SliceSeg), cudaMemcpyHostToDevice);
+      cudaError_t e1 = oz::launch_rowmax(dops, nullptr, (int)ops.size(), um, c->d_flags, 0);
+      cudaError_t e2 = oz::launch_digits(dops, nullptr, (int)ops.size(), ud, S, 0);
+      cudaError_t e3 = cudaDeviceSynchronize();
+      cudaFree(dops);
+      if (e1 != cudaSuccess) return bail(cuda_fail(e1, "operator rowmax"));
+      if (e2 != cudaSuccess) return bail(cuda_fail(e2, "operator digits"));
+      if (e3 != cudaSuccess) return bail(cuda_fail(e3, "operator slicing"));
+      int f[4];
+      cudaMemcpy(f, c->d_flags, 16, cudaMemcpyDeviceToHost);
+      if (f[0]) {
+        cudaMemset(c->d_flags, 0, 16);
+        return bail(fail(OZ_ENONFINITE, "an operator block held NaN or Inf"));
+      }
+    }
+
+    // ---- row tables of stage 1 (stacked L rows -> concatenated T layout of stage 2)
+    std::vector<long long> rowdst(A1row[nsec], 0);
+    std::vector<int> rowslot(A1row[nsec], 0);
+    for (int q = 0; q < nsec; ++q)
+      for (int t : bysrc[q]) {
+        int d = tasks[t].dst;
+        for (int i = 0; i < m[d]; ++i) {
+          long long r = A1row[q] + rowin1[t] + i;
+          rowdst[r] = stoff[d] + (long long)i * ld2[d] + offk[t];
+          rowslot[r] = (int)(A2row[d] + i);
+        }
+      }
+    long long* dRowdst;
+    int* dRowslot;
+    if ((rc = h->alloc(&dRowdst, rowdst.size() * 8))) return bail(rc);
+    if ((rc = h->alloc(&dRowslot, rowslot.size() * 4))) return bail(rc);
+    OZ_CU(cudaMemcpy(dRowdst, rowdst.data(), rowdst.size() * 8, cudaMemcpyHostToDevice));
+    OZ_CU(cudaMemcpy(dRowslot, rowslot.data(), rowslot.size() * 4, cudaMemcpyHostToDevice));
+
+    // ---- problems and tiles (larger k first; n-blocks of one m-block adjacent for L2 reuse)
+    std::vector<GemmProblem> p1, p2;
+    std::vector<int> ord1, ord2;
+    for (int q = 0; q < nsec; ++q) {
+      if (!bysrc[q].empty()) {
+        GemmProblem P{};
+        P.A = h->dA1 + A1off[q]; P.B = h->dB1 + B1off[q]; P.ea = eA1 + A1row[q]; P.eb = h->eB1 + B1row[q];
+        P.M = rows1[q]; P.N = n[q]; P.nkb = nkb1[q]; P.SA = S; P.SB = S; P.s = s;
+        P.mode = oz::OUT_ROWTABLE; P.C = h->dStage; P.ldc = 0;
+        P.rowdst = dRowdst + A1row[q]; P.rowslot = dRowslot + A1row[q]; P.rowmax = h->mA2;
+        P.alpha = 1.0; P.beta = 0.0;
+        p1.push_back(P);
+      }
+      if (!bydst[q].empty()) {
+        GemmProblem P{};
+        P.A = h->dA2 + A2off[q]; P.B = h->dB2 + B2off[q]; P.ea = h->eA2 + A2row[q]; P.eb = eB2 + B2row[q];
+        P.M = m[q]; P.N = n[q]; P.nkb = nkb2[q]; P.SA = S; P.SB = S; P.s = s;
+        P.mode = oz::OUT_DENSE; P.C = h->dY + h->psioff[q]; P.ldc = n[q];
+        P.alpha = 1.0; P.beta = 0.0;
+        p2.push_back(P);
+      }
+    }
+    auto make_tiles = [](const std::vector<GemmProblem>& ps) {
+      std::vector<int> ord(ps.size());
+      for (size_t i = 0; i < ps.size(); ++i) ord[i] = (int)i;
+      std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return ps[a].nkb > ps[b].nkb; });
+      std::vector<GemmTile> tl;
+      for (int pi : ord) {
+        int nrb = (int)cdiv(ps[pi].M, oz::TILE_M), nnb = (int)cdiv(ps[pi].N, oz::BN);
+        for (int mb = 0; mb < nrb; ++mb)
+          for (int nb = 0; nb < nnb; ++nb) tl.push_back({pi, mb, nb, 0});
+      }
+      return tl;
+    };
+    std::vector<GemmTile> t1 = make_tiles(p1), t2 = make_tiles(p2);
+    h->nt1 = (int)t1.size();
+    h->nt2 = (int)t2.size();
+    if ((rc = h->alloc(&h->dP1, std::max<size_t>(1, p1.size()) * sizeof(GemmProblem)))) return bail(rc);
+    if ((rc = h->alloc(&h->dP2, std::max<size_t>(1, p2.size()) * sizeof(GemmProblem)))) return bail(rc);
+    if ((rc = h->alloc(&h->dT1, std::max<size_t>(1, t1.size()) * sizeof(GemmTile)))) return bail(rc);
+    if ((rc = h->alloc(&h->dT2, std::max<size_t>(1, t2.size()) * sizeof(GemmTile)))) return bail(rc);
+    if (!p1.empty()) OZ_CU(cudaMemcpy(h->dP1, p1.data(), p1.size() * sizeof(GemmProblem), cudaMemcpyHostToDevice));
+    if (!p2.empty()) OZ_CU(cudaMemcpy(h->dP2, p2.data(), p2.size() * sizeof(GemmProblem), cudaMemcpyHostToDevice));
+    if (!t1.empty()) OZ_CU(cudaMemcpy(h->dT1, t1.data(), t1.size() * sizeof(GemmTile), cudaMemcpyHostToDevice));
+    if (!t2.empty()) OZ_CU(cudaMemcpy(h->dT2, t2.data(), t2.size() * sizeof(GemmTile), cudaMemcpyHostToDevice));
+
+    // ---- per-product slicing segments: psi (B of stage 1) and the concatenated T (A of stage 2)
+    std::vector<SliceSeg> sp, sa;
+    long long pm = 0, pd = 0, ad = 0;
+    for (int q = 0; q < nsec; ++q) {
+      if (bysrc[q].empty()) continue;
+      SliceSeg g{};
+      g.src = h->dPsi + h->psioff[q]; g.ld = n[q]; g.rows = n[q]; g.cols = m[q]; g.prows = g.rows; g.pcols = g.cols;
+      g.r0 = 0; g.k0 = 0; g.trans = 1; g.S = S; g.scale = 1.0;
+      g.dst = h->dB1 + B1off[q]; g.TR = oz::BN; g.nkb = nkb1[q];
+      g.rowmax = h->mB1 + B1row[q]; g.rowexp = h->eB1 + B1row[q];
+      g.unit0 = pd; g.unit0m = pm;
+      pd += oz::digit_units(g.prows, g.pcols);
+      pm += oz::rowmax_units(g.rows, g.cols);
+      sp.push_back(g);
+    }
+    for (int q = 0; q < nsec; ++q) {
+      if (bydst[q].empty()) continue;
+      SliceSeg g{};
+      g.src = h->dStage + stoff[q]; g.ld = ld2[q]; g.rows = m[q]; g.cols = ld2[q]; g.prows = g.rows;
+      g.pcols = g.cols; g.r0 = 0; g.k0 = 0; g.trans = 0; g.S = S; g.scale = 1.0;
+      g.dst = h->dA2 + A2off[q]; g.TR = oz::TILE_M; g.nkb = nkb2[q];
+      g.rowmax = h->mA2 + A2row[q]; g.rowexp = h->eA2 + A2row[q];
+      g.unit0 = ad; g.unit0m = 0;
+      ad += oz::digit_units(g.prows, g.pcols);
+      sa.push_back(g);
+    }
+    h->nsegPsi = (int)sp.size();
+    h->nsegA2 = (int)sa.size();
+    h->uPsiM = pm;
+    h->uPsiD = pd;
+    h->uA2D = ad;
+    if ((rc = h->alloc(&h->dSegPsi, std::max<size_t>(1, sp.size()) * sizeof(SliceSeg)))) return bail(rc);
+    if ((rc = h->alloc(&h->dSegA2, std::max<size_t>(1, sa.size()) * sizeof(SliceSeg)))) return bail(rc);
+    if (!sp.empty()) OZ_CU(cudaMemcpy(h->dSegPsi, sp.data(), sp.size() * sizeof(SliceSeg), cudaMemcpyHostToDevice));
+    if (!sa.empty()) OZ_CU(cudaMemcpy(h->dSegA2, sa.data(), sa.size() * sizeof(SliceSeg), cudaMemcpyHostToDevice));
+  }
+
+  // ---- CUDA graph of one product (psi and y are the handle's own buffers)
+  OZ_CU(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  if (mode == OZ_MODE_EAGER) {
+    // warm launch outside capture sets kernel attributes once (on a zero psi: no stale NaN patterns)
+    OZ_CU(cudaMemset(h->dPsi, 0, (size_t)h->dim * 8));
+    if ((rc = h->enqueue(h->cap))) return bail(rc);
+    OZ_CU(cudaStreamSynchronize(h->cap));
+    cudaGraph_t g;
+    OZ_CU(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    rc = h->enqueue(h->cap);
+    cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+    if (rc) return bail(rc);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamEndCapture"));
+    e = cudaGraphInstantiate(&h->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaGraphInstantiate"));
+  }
+  *out = h;
+  return OZ_OK;
+}
+
+extern "C" int oz_heff_destroy(oz_heff* h) {
+  if (!h) return OZ_OK;
+  cudaSetDevice(h->ctx->device);
+  cudaDeviceSynchronize();
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  for (void* p : h->allocs) cudaFree(p);
+  delete h;
+  return OZ_OK;
+}
+
+extern "C" int heff_apply(oz_heff* h, const double* psi, double* y, oz_stream_t stream) {
+  if (!h) return fail(OZ_EINVAL, "handle is null");
+  if (!psi || !y) return fail(OZ_EINVAL, "null vector");
+  if (psi == y) return fail(OZ_EINVAL, "y must not alias psi");
+  cudaStream_t st = (cudaStream_t)stream;
+  OZ_CU(cudaMemcpyAsync(h->dPsi, psi, (size_t)h->dim * 8, cudaMemcpyDeviceToDevice, st));
+  if (h->exec) {
+    OZ_CU(cudaGraphLaunch(h->exec, st));
+  } else if (int rc = h->enqueue(st)) {
+    return rc;
+  }
+  OZ_CU(cudaMemcpyAsync(y, h->dY, (size_t)h->dim * 8, cudaMemcpyDeviceToDevice, st));
+  return OZ_OK;
+}
+
+extern "C" int oz_heff_info_get(const oz_heff* h, oz_heff_info* o) {
+  if (!h || !o) return fail(OZ_EINVAL, "null argument");
+  o->dim = h->dim;
+  o->flops = h->flops;
+  o->carrier_flops = h->carrier_flops;
+  o->bytes_ops = h->bytes_ops;
+  o->bytes_scratch = h->bytes_scratch;
+  o->gemm1_tiles = h->nt1;
+  o->gemm2_tiles = h->nt2;
+  o->slices = h->S;
+  o->level = h->s;
+  o->mode = h->mode;
+  return OZ_OK;
+}

@@ -1,0 +1,227 @@
+// Shared device helpers: mbarriers, bulk async copies, tcgen05 (TMEM, MMA), descriptors.
+// Everything here is sm_103a inline PTX; nothing falls back to another architecture.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+
+#ifndef OZ_DEVICE_INLINE
+#define OZ_DEVICE_INLINE __device__ __forceinline__
+#endif
+
+namespace oz {
+
+// Digit tiles: K-blocks of 32 FP16 digits; "core matrices" of 8 rows x 8 K-elements
+// (128 contiguous bytes) in the no-swizzle K-major canonical layout of tcgen05.mma.
+constexpr int KB = 32;                 // K elements per k-block
+constexpr int KB_CM = KB / 8;          // core matrices along K in one k-block
+constexpr int TILE_M = 128;            // A-operand tile rows (MMA M)
+constexpr int GROUP_TERMS = 1008;      // products per FP32 accumulator group: 1008 * 2^14 < 2^24
+
+// element offset (in halves) of (r, k) inside one R x KB tile
+OZ_DEVICE_INLINE int tile_off(int r, int k) {
+  return (((r >> 3) * KB_CM + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
+}
+
+OZ_DEVICE_INLINE uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// ----------------------------------------------------------------------------------------------
+// mbarrier
+// ----------------------------------------------------------------------------------------------
+OZ_DEVICE_INLINE void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+OZ_DEVICE_INLINE void mbar_arrive(uint32_t a) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(a) : "memory");
+}
+OZ_DEVICE_INLINE void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(a), "r"(bytes)
+               : "memory");
+}
+OZ_DEVICE_INLINE bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.b32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Spin budget for every wait in the library's kernels (clock64 cycles, about 2 s at 2 GHz).
+constexpr long long WAIT_BUDGET = 1ll << 32;
+
+// Bounded wait.  Returns false (and never blocks again) once `abort` is set or the budget runs out.
+OZ_DEVICE_INLINE bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort) {
+  if (mbar_try(a, parity)) return true;
+  long long t0 = clock64();
+  while (true) {
+    if (mbar_try(a, parity)) return true;
+    if (*abort) return false;
+    if (clock64() - t0 > WAIT_BUDGET) {
+      *abort = 1;
+      return false;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------------------------
+// bulk async copy global -> shared (16-byte aligned, size multiple of 16)
+// ----------------------------------------------------------------------------------------------
+OZ_DEVICE_INLINE void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
+// ----------------------------------------------------------------------------------------------
+// tcgen05
+// ----------------------------------------------------------------------------------------------
+OZ_DEVICE_INLINE void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+OZ_DEVICE_INLINE void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+OZ_DEVICE_INLINE void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+OZ_DEVICE_INLINE void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+OZ_DEVICE_INLINE void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+// Shared-memory matrix descriptor, no swizzle, K-major: LBO = stride between core matrices
+// along K, SBO = stride between 8-row groups; bit 46 = descriptor version for tcgen05.
+OZ_DEVICE_INLINE uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// Instruction descriptor of kind::f16: D = F32, A = B = F16, both K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// collector usage for A: 0 none, 1 fill, 2 use, 3 lastuse
+template <int COL>
+OZ_DEVICE_INLINE void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  if constexpr (COL == 0)
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+  else if constexpr (COL == 1)
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, "
+        "%3, p;\n}" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+  else if constexpr (COL == 2)
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16.collector::a::use [%0], %1, %2, "
+        "%3, p;\n}" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+  else
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, "
+        "%2, %3, p;\n}" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+// 32 lanes x 32 columns of 32-bit TMEM words: thread i of the warp gets lane (base+i), 32 columns.
+OZ_DEVICE_INLINE void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%"
+      "20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+OZ_DEVICE_INLINE void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+OZ_DEVICE_INLINE void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ----------------------------------------------------------------------------------------------
+// exact integer <-> FP64 helpers (integer arithmetic only: FP64 units are scarce on this GPU)
+// ----------------------------------------------------------------------------------------------
+
+// Shared exponent of a row/column from the bit pattern of max|x|: the smallest e with
+// max|x| <= (127/128) 2^e; 0 for an all-zero row.
+OZ_DEVICE_INLINE int exponent_from_maxbits(unsigned long long mb) {
+  if (mb == 0ull) return 0;
+  int be = (int)(mb >> 52);
+  unsigned long long f = mb & ((1ull << 52) - 1);
+  if (be == 0) {  // subnormal: normalise so that the value is (1.f') 2^(-1022 - shift)
+    int lz = __clzll((long long)f) - 11;  // leading zeros within the 53-bit field (bit 52 empty)
+    f = (f << lz) & ((1ull << 52) - 1);
+    be = 1 - lz;
+  }
+  int ex = be - 1022;                      // value = m 2^ex with m in [0.5, 1)
+  return (f > (63ull << 46)) ? ex + 1 : ex;  // m <= 127/128  <=>  f <= 63 * 2^46
+}
+
+// RN_even(|x| * 2^sh) for the 53-bit significand M of x and a shift sh; exact integer result.
+OZ_DEVICE_INLINE unsigned long long round_shift(unsigned long long M, int sh) {
+  if (sh >= 0) return M << sh;               // caller guarantees no overflow
+  int r = -sh;
+  if (r >= 64) return 0ull;
+  unsigned long long q = M >> r;
+  unsigned long long rem = M & ((1ull << r) - 1);
+  unsigned long long half = 1ull << (r - 1);
+  if (rem > half || (rem == half && (q & 1ull))) ++q;
+  return q;
+}
+
+// RN_even(Z * 2^E) as IEEE binary64, Z a signed 128-bit integer.
+OZ_DEVICE_INLINE double int128_to_double(__int128 Z, int E) {
+  if (Z == 0) return 0.0;
+  unsigned long long sign = 0;
+  unsigned __int128 a;
+  if (Z < 0) {
+    sign = 1ull << 63;
+    a = (unsigned __int128)(-Z);
+  } else {
+    a = (unsigned __int128)Z;
+  }
+  unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
+  int nb = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);  // bit length
+  int e2 = nb - 1 + E;                                                        // binary exponent of leading bit
+  int drop;                                                                   // bits to drop from a
+  if (e2 >= -1022) {
+    drop = nb - 53;
+  } else {
+    drop = -1074 - E;  // keep bits at weight >= 2^-1074
+  }
+  unsigned long long mant;
+  if (drop <= 0) {
+    mant = (unsigned long long)(a << (-drop));
+  } else if (drop >= 128) {
+    return __longlong_as_double((long long)sign);  // far below half the smallest subnormal
+  } else {
+    unsigned __int128 q = a >> drop;
+    unsigned __int128 rem = a - (q << drop);
+    unsigned __int128 half = (unsigned __int128)1 << (drop - 1);
+    if (rem > half || (rem == half && (q & 1))) q += 1;
+    mant = (unsigned long long)q;
+  }
+  unsigned long long bits;
+  if (e2 >= -1022) {
+    if (mant >> 53) {  // rounding carried into a new bit
+      mant >>= 1;
+      e2 += 1;
+    }
+    if (e2 > 1023) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
+    bits = sign | ((unsigned long long)(e2 + 1023) << 52) | (mant & ((1ull << 52) - 1));
+  } else {
+    bits = sign | mant;  // subnormal (mant may reach 2^52: that is the smallest normal, encoded alike)
+  }
+  return __longlong_as_double((long long)bits);
+}
+
+}  // namespace oz

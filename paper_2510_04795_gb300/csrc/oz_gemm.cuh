@@ -1,0 +1,43 @@
+// Grouped persistent Ozaki GEMM on tcgen05 (declarations).
+#pragma once
+#include "oz_common.cuh"
+
+namespace oz {
+
+constexpr int BN = 64;              // output tile columns (MMA N)
+constexpr int NBUF = 512 / BN;      // TMEM accumulator buffers of BN columns
+constexpr int NSTAGE = 2;           // shared-memory pipeline stages
+constexpr int MAX_LEVEL = 8;        // slice levels supported by the BN = 64 kernel (one buffer per diagonal)
+constexpr int QN = 16;              // drain-record ring
+
+enum : int { OUT_DENSE = 0, OUT_ROWTABLE = 1 };
+
+// One emulated product C = alpha * (A B) + beta * C at slice level s.
+// A: M x K as tiled digit planes (TILE_M-row tiles), B^T: N x K as tiled planes (BN-row tiles).
+struct GemmProblem {
+  const __half* A;
+  const __half* B;
+  const int* ea;               // per A row exponent
+  const int* eb;               // per B^T row (output column) exponent
+  int M, N, nkb;               // sizes, k-blocks of 32
+  int SA, SB;                  // planes stored per k-block in A / B^T
+  int s;                       // slice level (1..MAX_LEVEL)
+  int mode;                    // OUT_DENSE or OUT_ROWTABLE
+  double* C;                   // dense: C + row * ldc + col;  rowtable: C + rowdst[row] + col
+  long long ldc;
+  const long long* rowdst;
+  const int* rowslot;
+  unsigned long long* rowmax;  // rowtable: max |C| per destination slot (atomicMax), may be null
+  double alpha, beta;
+};
+
+struct GemmTile {
+  int prob, mb, nb, pad;
+};
+
+size_t gemm_smem_bytes();
+// tiles == nullptr: a single problem (probs[0]) with implicit tiles i -> (i / nnb, i % nnb)
+cudaError_t launch_gemm(const GemmProblem* d_probs, const GemmTile* d_tiles, int ntiles, int grid,
+                        const GemmProblem* single, int* d_err, cudaStream_t st);
+
+}  // namespace oz

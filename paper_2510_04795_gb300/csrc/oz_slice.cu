@@ -1,0 +1,190 @@
+// Slicing kernels: the fixed-point conversion and 8-bit split of the Ozaki scheme
+// (paper, section "Theory of emulated FP64 arithmetic", steps 1 and 2; S slices carry
+// 8S-1 magnitude bits plus sign, section "Numerical procedure").
+//
+//  * rowmax pass: max |x| of every operand row (bit pattern, atomicMax), coalesced reads.
+//  * digit pass:  e = smallest integer with max|x| <= (127/128) 2^e;  X = RN_even(x 2^(8S-1-e));
+//                 balanced base-256 digits d_1..d_S in [-128,127]; each written as an FP16
+//                 value into the tcgen05 operand tiles (16-byte stores, 8 K-elements each).
+// Only integer operations touch the values after the (optional) scale multiply.
+#include "oz_slice.cuh"
+
+namespace oz {
+
+template <bool MAXPASS>
+__device__ __forceinline__ const SliceSeg& find_seg(const SliceSeg* segs, const SegPack& pack, int nseg,
+                                                    long long unit) {
+  const SliceSeg* base = segs ? segs : pack.seg;
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    long long u0 = MAXPASS ? base[mid].unit0m : base[mid].unit0;
+    if (u0 <= unit) lo = mid; else hi = mid - 1;
+  }
+  return base[lo];
+}
+
+__device__ __forceinline__ double load_src(const SliceSeg& g, int i, int j) {
+  long long off = g.trans ? (long long)j * g.ld + i : (long long)i * g.ld + j;
+  double v = __ldg(g.src + off);
+  return g.scale != 1.0 ? __dmul_rn(v, g.scale) : v;
+}
+
+__device__ __forceinline__ unsigned long long absbits(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+__global__ void __launch_bounds__(256) rowmax_kernel(const SliceSeg* __restrict__ segs,
+                                                     const __grid_constant__ SegPack pack, int nseg, long long total,
+                                                     int* __restrict__ flags) {
+  long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= total) return;
+  const SliceSeg& g = find_seg<true>(segs, pack, nseg, u);
+  long long lu = u - g.unit0m;
+  int i = (int)(lu % g.rows);
+  int sp = (int)(lu / g.rows);
+  int j0 = sp * ROWMAX_SPAN, j1 = min(g.cols, j0 + ROWMAX_SPAN);
+  unsigned long long mx = 0;
+  for (int j = j0; j < j1; ++j) {
+    unsigned long long b = absbits(load_src(g, i, j));
+    mx = b > mx ? b : mx;
+  }
+  if (mx >= 0x7FF0000000000000ull) atomicOr(flags, 1);  // Inf or NaN in the input
+  if (mx) atomicMax(g.rowmax + g.r0 + i, mx);
+}
+
+// fixed point of one value: X = RN_even(|x| 2^(8S-1-e)) with sign; S <= 8 (fits int64)
+__device__ __forceinline__ long long fixed_point64(double x, int e, int S) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  int be = (int)((b >> 52) & 0x7FF);
+  unsigned long long f = b & ((1ull << 52) - 1);
+  if (be == 0 && f == 0) return 0;
+  unsigned long long M = be ? (f | (1ull << 52)) : f;
+  int bee = be ? be : 1;
+  int sh = bee - 1075 + 8 * S - 1 - e;
+  long long X = (long long)round_shift(M, sh);
+  return (b >> 63) ? -X : X;
+}
+
+__device__ __forceinline__ __int128 fixed_point128(double x, int e, int S) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  int be = (int)((b >> 52) & 0x7FF);
+  unsigned long long f = b & ((1ull << 52) - 1);
+  if (be == 0 && f == 0) return 0;
+  unsigned long long M = be ? (f | (1ull << 52)) : f;
+  int bee = be ? be : 1;
+  int sh = bee - 1075 + 8 * S - 1 - e;
+  __int128 X = sh >= 0 ? ((__int128)M << sh) : (__int128)round_shift(M, sh);
+  return (b >> 63) ? -X : X;
+}
+
+template <int S>
+__global__ void __launch_bounds__(256) digits_kernel(const SliceSeg* __restrict__ segs,
+                                                     const __grid_constant__ SegPack pack, int nseg, long long total) {
+  long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long u = tid >> 3;
+  if (u >= total) return;
+  int r8 = (int)(tid & 7);
+  const SliceSeg& g = find_seg<false>(segs, pack, nseg, u);
+  long long lu = u - g.unit0;
+  int nkc = (g.pcols + 7) >> 3;
+  int rg = (int)(lu / nkc), c = (int)(lu % nkc);
+  int i = rg * 8 + r8;
+  if (i >= g.prows) return;
+  int R = g.r0 + i;
+  const bool rowok = i < g.rows;
+  int e = rowok ? exponent_from_maxbits(g.rowmax[R]) : 0;
+  if (c == 0) g.rowexp[R] = e;
+  int d[S][8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    int j = c * 8 + q;
+    double v = (rowok && j < g.cols) ? load_src(g, i, j) : 0.0;
+    if constexpr (S <= 8) {
+      long long X = fixed_point64(v, e, S);
+#pragma unroll
+      for (int t = S - 1; t >= 0; --t) {
+        int dd = (int)((X + 128) & 255) - 128;
+        d[t][q] = dd;
+        X = (X - dd) >> 8;
+      }
+    } else {
+      __int128 X = fixed_point128(v, e, S);
+#pragma unroll
+      for (int t = S - 1; t >= 0; --t) {
+        int dd = (int)((X + 128) & 255) - 128;
+        d[t][q] = dd;
+        X = (X - dd) >> 8;
+      }
+    }
+  }
+  int K = g.k0 + c * 8;
+  int rt = R / g.TR, rr = R % g.TR, kb = K >> 5, kk = K & 31;
+  long long base = (((long long)rt * g.nkb + kb) * g.S) * (long long)(g.TR * KB) + tile_off(rr, kk);
+#pragma unroll
+  for (int t = 0; t < S; ++t) {
+    __half2 h0 = __halves2half2(__int2half_rn(d[t][0]), __int2half_rn(d[t][1]));
+    __half2 h1 = __halves2half2(__int2half_rn(d[t][2]), __int2half_rn(d[t][3]));
+    __half2 h2 = __halves2half2(__int2half_rn(d[t][4]), __int2half_rn(d[t][5]));
+    __half2 h3 = __halves2half2(__int2half_rn(d[t][6]), __int2half_rn(d[t][7]));
+    uint4 w;
+    w.x = *reinterpret_cast<uint32_t*>(&h0);
+    w.y = *reinterpret_cast<uint32_t*>(&h1);
+    w.z = *reinterpret_cast<uint32_t*>(&h2);
+    w.w = *reinterpret_cast<uint32_t*>(&h3);
+    *reinterpret_cast<uint4*>(g.dst + base + (long long)t * (g.TR * KB)) = w;
+  }
+}
+
+long long rowmax_units(int rows, int cols) {
+  return (long long)rows * ((cols + ROWMAX_SPAN - 1) / ROWMAX_SPAN);
+}
+long long digit_units(int prows, int pcols) { return (long long)((prows + 7) / 8) * ((pcols + 7) / 8); }
+
+cudaError_t launch_rowmax(const SliceSeg* d_segs, const SegPack* pack, int nseg, long long total, int* flags,
+                          cudaStream_t st) {
+  if (total <= 0) return cudaSuccess;
+  SegPack p{};
+  if (!d_segs) p = *pack;
+  long long blocks = (total + 255) / 256;
+  rowmax_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_segs, p, nseg, total, flags);
+  return cudaGetLastError();
+}
+
+__global__ void untile_kernel(const __half* __restrict__ dig, int TR, int nkb, int S, int rows, int cols,
+                              int8_t* __restrict__ out) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long total = (long long)S * rows * cols;
+  if (idx >= total) return;
+  int j = (int)(idx % cols);
+  int i = (int)((idx / cols) % rows);
+  int t = (int)(idx / ((long long)rows * cols));
+  int rt = i / TR, rr = i % TR, kb = j >> 5, kk = j & 31;
+  long long off = (((long long)rt * nkb + kb) * S + t) * (long long)(TR * KB) + tile_off(rr, kk);
+  out[idx] = (int8_t)__half2int_rn(dig[off]);
+}
+
+cudaError_t launch_untile(const __half* dig, int TR, int nkb, int S, int rows, int cols, int8_t* out,
+                          cudaStream_t st) {
+  long long total = (long long)S * rows * cols;
+  if (total <= 0) return cudaSuccess;
+  untile_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(dig, TR, nkb, S, rows, cols, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_digits(const SliceSeg* d_segs, const SegPack* pack, int nseg, long long total, int S,
+                          cudaStream_t st) {
+  if (total <= 0) return cudaSuccess;
+  SegPack p{};
+  if (!d_segs) p = *pack;
+  long long blocks = (total * 8 + 255) / 256;
+  switch (S) {
+#define OZ_CASE(s) case s: digits_kernel<s><<<(unsigned)blocks, 256, 0, st>>>(d_segs, p, nseg, total); break;
+    OZ_CASE(1) OZ_CASE(2) OZ_CASE(3) OZ_CASE(4) OZ_CASE(5) OZ_CASE(6) OZ_CASE(7) OZ_CASE(8) OZ_CASE(9)
+#undef OZ_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace oz

@@ -1,0 +1,105 @@
+"""GPU parity of heff_apply against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import synthetic
+from oracle import heff
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2510_04795_gb300 as oz
+    c = oz.Context(0)
+    yield c
+    c.close()
+
+
+def _problem(grid, dims, nterms, spread, seed=1, device="cuda"):
+    st = synthetic.heff_structure(grid=grid, dims=dims, nterms=nterms, spread=spread, seed=seed)
+    blocks = [synthetic.gen_task_blocks(st, t, device=device) for t in range(st.ntask)]
+    psi = synthetic.gen_psi(st, device=device)
+    return st, blocks, psi
+
+
+def _tasks(st, blocks):
+    return [(int(s), int(d), float(st.term_coef[k]), L, R) for (k, s, d), (L, R) in zip(st.tasks, blocks)]
+
+
+@pytest.mark.parametrize("seed,grid,dims,S,s", [(1, (3, 3), (2, 20), 7, 7), (2, (4, 3), (5, 70), 4, 4),
+                                               (3, (3, 2), (60, 140), 9, 6)])
+def test_heff_bitexact_vs_emulated_oracle(ctx, seed, grid, dims, S, s):
+    import paper_2510_04795_gb300 as oz
+    st, blocks, psi = _problem(grid, dims, 8, True, seed)
+    h = oz.Heff(ctx, st.m, st.n, _tasks(st, blocks), slices=S, level=s)
+    y = h.apply(psi)
+    ctx.status()
+    Lb = [b[0].cpu().numpy() for b in blocks]
+    Rb = [b[1].cpu().numpy() for b in blocks]
+    ref = heff.heff_apply_emulated(st, Lb, Rb, psi.cpu().numpy(), S, s)
+    got = y.cpu().numpy()
+    assert np.array_equal(got.view(np.int64), ref.view(np.int64))
+    h.close()
+
+
+def test_heff_repeatable_and_graph_replay(ctx):
+    import paper_2510_04795_gb300 as oz
+    st, blocks, psi = _problem((4, 4), (4, 60), 16, True, 5)
+    h = oz.Heff(ctx, st.m, st.n, _tasks(st, blocks), slices=7)
+    y1 = h.apply(psi).clone()
+    y2 = h.apply(psi * 2.0)
+    y3 = h.apply(psi)
+    ctx.status()
+    assert torch.equal(y1, y3)
+    assert torch.equal(y2, 2.0 * y1)    # scaling psi by 2 scales every exponent exactly
+    h.close()
+
+
+def test_heff_40_blocks_slice_sweep(ctx):
+    """40 sector blocks of 8..256, 128 terms, six-decade exponent spread: error vs FP64 per slice count."""
+    import paper_2510_04795_gb300 as oz
+    st, blocks, psi = _problem((8, 5), (8, 256), 128, True, 1)
+    Lb = [b[0].cpu().numpy() for b in blocks]
+    Rb = [b[1].cpu().numpy() for b in blocks]
+    yref = heff.heff_apply_fp64(st, Lb, Rb, psi.cpu().numpy())
+    errs = {}
+    for s in (3, 4, 5, 6, 7, 8):
+        h = oz.Heff(ctx, st.m, st.n, _tasks(st, blocks), slices=s)
+        y = h.apply(psi)
+        ctx.status()
+        errs[s] = heff.rel_frobenius(y.cpu().numpy(), yref)
+        h.close()
+    print("rel Frobenius error by slice count:", errs)
+    assert errs[7] <= 1e-12
+    assert errs[8] <= 1e-13
+    for a, b in zip((3, 4, 5), (4, 5, 6)):
+        assert errs[b] < errs[a]
+
+
+def test_heff_native_mode(ctx):
+    import paper_2510_04795_gb300 as oz
+    st, blocks, psi = _problem((5, 4), (8, 100), 32, True, 7)
+    h = oz.Heff(ctx, st.m, st.n, _tasks(st, blocks), mode="native")
+    y = h.apply(psi)
+    ctx.status()
+    Lb = [b[0].cpu().numpy() for b in blocks]
+    Rb = [b[1].cpu().numpy() for b in blocks]
+    yref = heff.heff_apply_fp64(st, Lb, Rb, psi.cpu().numpy())
+    assert heff.rel_frobenius(y.cpu().numpy(), yref) < 1e-14
+    h.close()
+
+
+def test_heff_symmetric(ctx):
+    import paper_2510_04795_gb300 as oz
+    st, blocks, psi = _problem((4, 3), (4, 40), 16, False, 9)
+    h = oz.Heff(ctx, st.m, st.n, _tasks(st, blocks), slices=7)
+    g = torch.Generator(device="cpu").manual_seed(0)
+    x = torch.randn(h.dim, dtype=torch.float64, generator=g).cuda()
+    z = torch.randn(h.dim, dtype=torch.float64, generator=g).cuda()
+    hx, hz = h.apply(x).clone(), h.apply(z).clone()
+    ctx.status()
+    lhs, rhs = float(x @ hz), float(hx @ z)
+    assert abs(lhs - rhs) <= 1e-13 * float(hx.norm() * z.norm())
+    h.close()
