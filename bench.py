@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Throughput of the emulated-FP64 block-sparse two-site H_eff * psi on GB300.
+
+One step = one H_eff * psi product over the whole synthetic sector structure (all slicing and
+GEMM stages).  Workload (default): 300 U(1)xU(1) sector blocks of log-uniform size 16..1024,
+about 200 operator terms in transpose pairs, N(0,1)-like entries, S = 7 slices.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "effective FP64 TFLOP/s of H_eff*psi (Ozaki-INT8 vs native FP64) at |dE|<=1e-6 Eh"
+UNIT = "TFLOP/s"
+FALLBACK_PEAK = {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0}
+
+# DRAM bytes per algorithmic carrier flop of the GEMM kernel, from one ncu capture, and the
+# digest of the kernel source it was taken on (the figure is dropped once the source changes).
+NCU_TRAFFIC = {"bytes_per_carrier_flop": None, "gemm_source_sha256": None}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--config", default="heff300_16-1024")
+    p.add_argument("--nterms", type=int, default=None, help="override the term count (profiling runs)")
+    p.add_argument("--slices", type=int, default=7)
+    p.add_argument("--native-steps", type=int, default=1)
+    p.add_argument("--no-native", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return FALLBACK_PEAK, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.dev = device
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", delete=False, suffix=".csv")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [ln.strip().split(", ") for ln in self.f.read().splitlines() if ln.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[4:8]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gemm_source_digest() -> str:
+    h = hashlib.sha256()
+    for f in ("oz_gemm.cu", "oz_gemm.cuh", "oz_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2510_04795_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def structure(args):
+    import synthetic
+    cfg = dict(synthetic.CONFIGS[args.config])
+    if args.nterms:
+        cfg["nterms"] = args.nterms
+    return synthetic.heff_structure(**cfg), cfg
+
+
+def cpu_sample(st, budget_s: float, device: str):
+    """A bounded sample of the workload for the CPU oracle: the tasks of the first target sectors
+    (in sector order) until their FP64 flops reach about budget_s at the measured rate."""
+    import numpy as np
+    import synthetic
+    t = st.tasks
+    fl = 2 * (st.m[t[:, 2]].astype(np.int64) * st.m[t[:, 1]] * st.n[t[:, 1]]
+              + st.m[t[:, 2]].astype(np.int64) * st.n[t[:, 1]] * st.n[t[:, 2]])
+
+    def take(target):
+        sel, tot = [], 0
+        for q in range(st.nsec):
+            ids = np.nonzero(t[:, 2] == q)[0]
+            sel.extend(ids.tolist())
+            tot += int(fl[ids].sum())
+            if tot >= target:
+                break
+        return np.array(sel, dtype=np.int64), tot
+
+    def build(sel):
+        sub = synthetic.HeffStructure(st.labels, st.m, st.n, st.term_delta, st.term_coef, t[sel], st.spread,
+                                      st.seed)
+        Lb, Rb = [], []
+        for i in sel:
+            L, R = synthetic.gen_task_blocks(st, int(i), device=device)
+            Lb.append(L.cpu().numpy())
+            Rb.append(R.cpu().numpy())
+        return sub, Lb, Rb
+    return take, build
+
+
+def run_oracle_sample(st, budget_s, device):
+    from oracle import heff as OH
+    import synthetic
+    take, build = cpu_sample(st, budget_s, device)
+    psi = synthetic.gen_psi(st, device=device).cpu().numpy()
+    sel, fl = take(2e9)                          # calibration
+    sub, Lb, Rb = build(sel)
+    t0 = time.perf_counter()
+    OH.heff_apply_fp64(sub, Lb, Rb, psi)
+    rate = fl / max(time.perf_counter() - t0, 1e-6)
+    sel, fl = take(rate * budget_s)
+    sub, Lb, Rb = build(sel)
+    return sub, Lb, Rb, psi, fl
+
+
+def reference_arm(args):
+    """--impl reference: the CPU oracle, as it stands, on a bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import heff as OH
+    st, cfg = structure(args)
+    dev = "cuda" if _has_cuda() else "cpu"
+    sub, Lb, Rb, psi, fl = run_oracle_sample(st, min(args.cpu_seconds, 6.0), dev)
+    for _ in range(args.warmup):
+        OH.heff_apply_fp64(sub, Lb, Rb, psi)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        OH.heff_apply_fp64(sub, Lb, Rb, psi)
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    v = fl / dt / 1e12
+    sample = (f"{sub.ntask} of {st.ntask} tasks (all tasks into the first target sectors), "
+              f"{fl:.3e} FP64 flop per step, numpy per-block products")
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_config(args, st, cfg),
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def _has_cuda():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def workload_config(args, st, cfg):
+    return {"workload": f"{args.config}_s{args.slices}", "sector_blocks": st.nsec,
+            "block_dims": f"{cfg['dims'][0]}-{cfg['dims'][1]} log-uniform", "terms": len(st.term_coef),
+            "tasks": st.ntask, "slices": args.slices, "psi_dim": int(st.psi_offsets()[-1]),
+            "fp64_flop_per_step": st.flops(), "entries": "exponent spread 2^-j" if st.spread else "N(0,1)-like",
+            "l2": "inputs larger than L2 (operator digit planes are > 100 GB)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import synthetic
+    import paper_2510_04795_gb300 as oz
+
+    ctx = oz.Context(local)
+    st, cfg = structure(args)
+    F = st.flops()
+    S = args.slices
+    P = S * (S + 1) // 2
+
+    Lbuf, Rbuf, Lo, Ro = synthetic.gen_all_task_blocks(st, device="cuda")
+    tasks = []
+    for i, (k, s, d) in enumerate(st.tasks):
+        L = Lbuf[Lo[i]:Lo[i + 1]].view(int(st.m[d]), int(st.m[s]))
+        R = Rbuf[Ro[i]:Ro[i + 1]].view(int(st.n[d]), int(st.n[s]))
+        tasks.append((int(s), int(d), float(st.term_coef[k]), L, R))
+    psi = synthetic.gen_psi(st, device="cuda")
+    torch.cuda.synchronize()
+
+    native = None
+    y_nat = None
+    if rank == 0 and not args.no_native:
+        hn = oz.Heff(ctx, st.m, st.n, tasks, mode="native")
+        y_nat = hn.apply(psi)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.native_steps):
+            hn.apply(psi, y_nat)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.native_steps
+        native = {"value": F / (ms * 1e-3) / 1e12, "unit": UNIT, "ms_per_step": ms, "steps": args.native_steps,
+                  "path": "cuBLAS DGEMM (default math, no emulation) on the same stacked task list"}
+        hn.close()
+        del hn
+        torch.cuda.empty_cache()
+
+    h = oz.Heff(ctx, st.m, st.n, tasks, slices=S)
+    del tasks, Lbuf, Rbuf
+    torch.cuda.empty_cache()
+    info = h.info()
+    y = torch.empty_like(psi)
+    for _ in range(args.warmup):
+        h.apply(psi, y)
+    ctx.status()
+
+    clocks = Clocks(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stage = [0.0, 0.0, 0.0, 0.0]
+    e0.record()
+    for _ in range(args.steps):
+        h.apply(psi, y)
+        for i, v in enumerate(oz.heff_stage_times(h)):
+            stage[i] += v
+    e1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ctx.status()
+    stage = [v / args.steps for v in stage]
+
+    # accuracy against the native FP64 product of the same task list
+    rel_native = None
+    if y_nat is not None:
+        rel_native = float(torch.linalg.vector_norm(y - y_nat) / torch.linalg.vector_norm(y_nat))
+
+    # end to end through the C ABI with page-locked host vectors (copies inside the timed region)
+    psi_h = psi.cpu().pin_memory()
+    y_h = torch.empty_like(psi_h).pin_memory()
+    oz.heff_apply_host(h, psi_h, y_h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oz.heff_apply_host(h, psi_h, y_h)
+        torch.cuda.current_stream().synchronize()
+    ms_e2e = (time.perf_counter() - t0) * 1e3 / args.steps
+    if world > 1:
+        t = torch.tensor([ms_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    ok_e2e = bool(torch.equal(y_h, y.cpu()))
+
+    pk, pk_src = peaks()
+    peak = float(pk.get("bf16_tflops_sustained", FALLBACK_PEAK["bf16_tflops_sustained"]))
+    gemm_ms = stage[1] + stage[3]
+    achieved = P * F / (gemm_ms * 1e-3) / 1e12
+    traffic = None
+    if NCU_TRAFFIC["bytes_per_carrier_flop"] and NCU_TRAFFIC["gemm_source_sha256"] == gemm_source_digest():
+        traffic = NCU_TRAFFIC["bytes_per_carrier_flop"] * P * F / 2  # per launch (two launches per step)
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": "oz::gemm_kernel (tcgen05.mma kind::f16, INT8 digits carried in FP16)",
+            "algorithmic": f"s(s+1)/2 * sum_tasks 2(m'mn+m'nn') = {P}*{F:.4e} flop per step over 2 launches",
+            "peak_source": f"bf16_tflops_sustained ({pk_src}); fp16 and bf16 share the nominal rate"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        from oracle import heff as OH
+        sub, Lb, Rb, psi_c, fl = run_oracle_sample(st, args.cpu_seconds, "cuda")
+        t0 = time.perf_counter()
+        OH.heff_apply_fp64(sub, Lb, Rb, psi_c)
+        dt = time.perf_counter() - t0
+        cpu = {"value": fl / dt / 1e12, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{sub.ntask} of {st.ntask} tasks (all tasks into the first target sectors), "
+                         f"{fl:.3e} FP64 flop, {dt:.1f} s, numpy per-block products on the host BLAS"}
+
+    value = world * F / (ms * 1e-3) / 1e12
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(workload_config(args, st, cfg), parallelism=f"replicas x{world}"),
+        "e2e": {"value": world * F / (ms_e2e * 1e-3) / 1e12, "unit": UNIT, "h2d_bytes_per_step": int(psi.numel() * 8),
+                "d2h_bytes_per_step": int(psi.numel() * 8), "matches_device_result": ok_e2e},
+        "gpu_launches": 5 * args.steps,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "native_fp64": native,
+        "rel_frobenius_vs_native_fp64": rel_native,
+        "stages_ms": {"slice_psi": stage[0], "gemm_stage1": stage[1], "slice_T": stage[2], "gemm_stage2": stage[3]},
+        "carrier_flop_per_step_padded": info["carrier_flops"],
+        "device_bytes": {"operators": info["bytes_ops"], "scratch": info["bytes_scratch"]},
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    h.close()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -131,6 +131,14 @@ int oz_heff_create(oz_ctx* ctx, int nsec, const int* m, const int* n, int ntask,
 int oz_heff_destroy(oz_heff* h);
 /* d_y = H_eff d_psi (flat block vectors of length sum m[q] n[q]; d_y must not alias d_psi). */
 int heff_apply(oz_heff* h, const double* d_psi, double* d_y, oz_stream_t stream);
+/* End-to-end form of heff_apply on HOST vectors: copies psi_host to the device, applies H_eff,
+ * copies the result to y_host, all enqueued on `stream` (page-locked host memory makes the copies
+ * asynchronous; pageable memory works but serialises them). */
+int heff_apply_host(oz_heff* h, const double* psi_host, double* y_host, oz_stream_t stream);
+/* Device durations (ms) of the stages of the last heff_apply / heff_apply_host of an EAGER handle,
+ * from CUDA events recorded on its stream: [0] slicing of psi, [1] stage-1 GEMM launch,
+ * [2] slicing of the intermediate, [3] stage-2 GEMM launch.  Waits for that product to finish. */
+int oz_heff_stage_times(oz_heff* h, float* ms4);
 /* Sizes and bookkeeping of the handle. */
 typedef struct oz_heff_info {
   long long dim;          /* length of psi */

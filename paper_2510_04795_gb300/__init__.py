@@ -14,6 +14,7 @@ from . import _native as N
 from ._native import OzError, OZ_MODE_EAGER, OZ_MODE_NATIVE
 
 __all__ = ["Context", "Heff", "OzError", "ozaki_gemm", "ozaki_slice", "ozaki_slice_products", "heff_apply",
+           "heff_apply_host", "heff_stage_times",
            "OZ_MODE_EAGER", "OZ_MODE_NATIVE"]
 
 
@@ -155,6 +156,21 @@ class Heff:
             y = torch.empty_like(psi)
         N.check(self.lib.heff_apply(self.h, _ptr(psi), _ptr(y), _stream(stream)))
         return y
+
+
+def heff_apply_host(h: Heff, psi_host: torch.Tensor, y_host: torch.Tensor, stream=None) -> torch.Tensor:
+    """End-to-end product on host (preferably pinned) float64 tensors."""
+    if psi_host.is_cuda or y_host.is_cuda or psi_host.dtype != torch.float64 or y_host.dtype != torch.float64:
+        raise OzError(N.OZ_EINVAL, "expected host float64 tensors")
+    N.check(h.lib.heff_apply_host(h.h, psi_host.data_ptr(), y_host.data_ptr(), _stream(stream)))
+    return y_host
+
+
+def heff_stage_times(h: Heff) -> list:
+    """Device ms of [psi slicing, stage-1 GEMM, intermediate slicing, stage-2 GEMM] of the last product."""
+    arr = (C.c_float * 4)()
+    N.check(h.lib.oz_heff_stage_times(h.h, arr))
+    return [float(x) for x in arr]
 
 
 def heff_apply(h: Heff, psi: torch.Tensor, y: torch.Tensor | None = None, stream=None) -> torch.Tensor:

@@ -73,6 +73,8 @@ def load():
         "oz_heff_destroy": (i, [vp]),
         "heff_apply": (i, [vp, vp, vp, vp]),
         "oz_heff_info_get": (i, [vp, C.POINTER(oz_heff_info)]),
+        "heff_apply_host": (i, [vp, vp, vp, vp]),
+        "oz_heff_stage_times": (i, [vp, C.POINTER(C.c_float)]),
         "oz_heff_diag": (i, [vp, vp, vp]),
         "davidson_step": (i, [vp, vp, vp, C.POINTER(oz_davidson_result), vp]),
         "davidson_solve": (i, [vp, vp, C.POINTER(oz_davidson_opts), C.POINTER(oz_davidson_result), vp]),

@@ -310,8 +310,17 @@ struct oz_heff_s {
   long long nTrows = 0;
 
   double *dPsi = nullptr, *dY = nullptr;
+  bool prepared = false;
+  // layout kept for the lazy per-product setup of the emulated path
+  std::vector<std::vector<int>> bysrc, bydst;
+  std::vector<int> rows1, nkb1, nkb2, ld2, tsrc, tdst;
+  std::vector<long long> offk, rowin1, stoff, A1off, B1off, A2off, B2off, A1row, B1row, A2row, B2row;
+  int* eA1 = nullptr;
+  int* eB2 = nullptr;
+  int prepare();
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // stage boundaries of the last product
 
   template <class T>
   int alloc(T** p, size_t bytes) {
@@ -322,7 +331,7 @@ struct oz_heff_s {
     allocs.push_back((void*)*p);
     return OZ_OK;
   }
-  int enqueue(cudaStream_t st);
+  int enqueue(cudaStream_t st, bool capturing = false);
 };
 
 namespace {
@@ -337,16 +346,23 @@ __global__ void scatter_rows_kernel(const double* __restrict__ T, const long lon
 }
 }  // namespace
 
-int oz_heff_s::enqueue(cudaStream_t st) {
+int oz_heff_s::enqueue(cudaStream_t st, bool capturing) {
+  const unsigned evf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (mode == OZ_MODE_EAGER) {
+    // events are recorded as graph nodes when captured (external record), plain records otherwise
+    OZ_CU(cudaEventRecordWithFlags(ev[0], st, evf));
     if (bytes_mB1) OZ_CU(cudaMemsetAsync(mB1, 0, bytes_mB1, st));
     if (bytes_mA2) OZ_CU(cudaMemsetAsync(mA2, 0, bytes_mA2, st));
     OZ_CU(oz::launch_rowmax(dSegPsi, nullptr, nsegPsi, uPsiM, ctx->d_flags, st));
     OZ_CU(oz::launch_digits(dSegPsi, nullptr, nsegPsi, uPsiD, S, st));
+    OZ_CU(cudaEventRecordWithFlags(ev[1], st, evf));
     OZ_CU(oz::launch_gemm(dP1, dT1, nt1, ctx->nsm, nullptr, ctx->d_flags + 1, st));
+    OZ_CU(cudaEventRecordWithFlags(ev[2], st, evf));
     OZ_CU(oz::launch_digits(dSegA2, nullptr, nsegA2, uA2D, S, st));
     if (zero_y) OZ_CU(cudaMemsetAsync(dY, 0, (size_t)dim * 8, st));
+    OZ_CU(cudaEventRecordWithFlags(ev[3], st, evf));
     OZ_CU(oz::launch_gemm(dP2, dT2, nt2, ctx->nsm, nullptr, ctx->d_flags + 1, st));
+    OZ_CU(cudaEventRecordWithFlags(ev[4], st, evf));
     return OZ_OK;
   }
   // native FP64: one DGEMM per source sector, scatter into the concatenated layout, one per target
@@ -472,13 +488,13 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
   }
 
   int rc;
-  if ((rc = h->alloc(&h->dPsi, (size_t)h->dim * 8))) return bail(rc);
-  if ((rc = h->alloc(&h->dY, (size_t)h->dim * 8))) return bail(rc);
-  if ((rc = h->alloc(&h->dStage, (size_t)stoff[nsec] * 8))) return bail(rc);
-  OZ_CU(cudaMemset(h->dStage, 0, (size_t)stoff[nsec] * 8));
   h->bytes_scratch = (long long)stoff[nsec] * 8 + 2 * h->dim * 8;
 
   if (mode == OZ_MODE_NATIVE) {
+    if ((rc = h->alloc(&h->dPsi, (size_t)h->dim * 8))) return bail(rc);
+    if ((rc = h->alloc(&h->dY, (size_t)h->dim * 8))) return bail(rc);
+    if ((rc = h->alloc(&h->dStage, (size_t)stoff[nsec] * 8))) return bail(rc);
+    OZ_CU(cudaMemset(h->dStage, 0, (size_t)stoff[nsec] * 8));
     // stacked FP64 copies: A1 (per source: rows1 x m[q]) and B2T (per target: n[q] x ld2, zero padded)
     std::vector<long long> a1o(nsec + 1, 0), b2o(nsec + 1, 0), to(nsec + 1, 0);
     for (int q = 0; q < nsec; ++q) {
@@ -529,12 +545,8 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
     // ---- device buffers of the emulated path
     size_t bA1 = A1off[nsec] * 2, bB1 = B1off[nsec] * 2, bA2 = A2off[nsec] * 2, bB2 = B2off[nsec] * 2;
     if ((rc = h->alloc(&h->dA1, bA1))) return bail(rc);
-    if ((rc = h->alloc(&h->dB1, bB1))) return bail(rc);
-    if ((rc = h->alloc(&h->dA2, bA2))) return bail(rc);
     if ((rc = h->alloc(&h->dB2, bB2))) return bail(rc);
     OZ_CU(cudaMemset(h->dA1, 0, bA1));
-    OZ_CU(cudaMemset(h->dB1, 0, bB1));
-    OZ_CU(cudaMemset(h->dA2, 0, bA2));
     OZ_CU(cudaMemset(h->dB2, 0, bB2));
     h->bytes_ops = (long long)(bA1 + bB2);
     h->bytes_scratch += (long long)(bB1 + bA2);
@@ -542,14 +554,8 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
     unsigned long long *mA1, *mB2;
     if ((rc = h->alloc(&eA1, A1row[nsec] * 4))) return bail(rc);
     if ((rc = h->alloc(&eB2, B2row[nsec] * 4))) return bail(rc);
-    if ((rc = h->alloc(&h->eB1, B1row[nsec] * 4))) return bail(rc);
-    if ((rc = h->alloc(&h->eA2, A2row[nsec] * 4))) return bail(rc);
     if ((rc = h->alloc(&mA1, A1row[nsec] * 8))) return bail(rc);
     if ((rc = h->alloc(&mB2, B2row[nsec] * 8))) return bail(rc);
-    h->bytes_mB1 = B1row[nsec] * 8;
-    h->bytes_mA2 = A2row[nsec] * 8;
-    if ((rc = h->alloc(&h->mB1, h->bytes_mB1))) return bail(rc);
-    if ((rc = h->alloc(&h->mA2, h->bytes_mA2))) return bail(rc);
     OZ_CU(cudaMemset(mA1, 0, A1row[nsec] * 8));
     OZ_CU(cudaMemset(mB2, 0, B2row[nsec] * 8));
 
@@ -602,12 +608,60 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
       }
     }
 
+    h->eA1 = eA1;
+    h->eB2 = eB2;
+  }
+  h->bysrc = std::move(bysrc);
+  h->bydst = std::move(bydst);
+  h->rows1 = rows1; h->nkb1 = nkb1; h->nkb2 = nkb2; h->ld2 = ld2;
+  h->offk = offk; h->rowin1 = rowin1; h->stoff = stoff;
+  h->A1off = A1off; h->B1off = B1off; h->A2off = A2off; h->B2off = B2off;
+  h->A1row = A1row; h->B1row = B1row; h->A2row = A2row; h->B2row = B2row;
+  h->tsrc.resize(ntask); h->tdst.resize(ntask);
+  for (int t = 0; t < ntask; ++t) { h->tsrc[t] = tasks[t].src; h->tdst[t] = tasks[t].dst; }
+  for (auto& e : h->ev) OZ_CU(cudaEventCreate(&e));
+  if (mode == OZ_MODE_NATIVE) h->prepared = true;
+  *out = h;
+  return OZ_OK;
+}
+
+
+// Per-product buffers, tables, slicing segments and the CUDA graph of the emulated path.  Done on
+// the first product so that the caller can free its FP64 operator blocks after oz_heff_create.
+int oz_heff_s::prepare() {
+  if (prepared) return OZ_OK;
+  int rc;
+  const int nsec = this->nsec;
+  oz_ctx* c = ctx;
+  const std::vector<int>& m = this->m;
+  const std::vector<int>& n = this->n;
+  const int S = this->S, s = this->s, mode = this->mode;
+  (void)mode;
+  int* eA1 = this->eA1;
+  int* eB2 = this->eB2;
+  (void)c;
+  if ((rc = alloc(&dPsi, (size_t)dim * 8))) return rc;
+  if ((rc = alloc(&dY, (size_t)dim * 8))) return rc;
+  if ((rc = alloc(&dStage, (size_t)stoff[nsec] * 8))) return rc;
+  OZ_CU(cudaMemset(dStage, 0, (size_t)stoff[nsec] * 8));
+  size_t bB1 = B1off[nsec] * 2, bA2 = A2off[nsec] * 2;
+  if ((rc = alloc(&dB1, bB1))) return rc;
+  if ((rc = alloc(&dA2, bA2))) return rc;
+  OZ_CU(cudaMemset(dB1, 0, bB1));
+  OZ_CU(cudaMemset(dA2, 0, bA2));
+  if ((rc = alloc(&eB1, B1row[nsec] * 4))) return rc;
+  if ((rc = alloc(&eA2, A2row[nsec] * 4))) return rc;
+  bytes_mB1 = B1row[nsec] * 8;
+  bytes_mA2 = A2row[nsec] * 8;
+  if ((rc = alloc(&mB1, bytes_mB1))) return rc;
+  if ((rc = alloc(&mA2, bytes_mA2))) return rc;
+  {
     // ---- row tables of stage 1 (stacked L rows -> concatenated T layout of stage 2)
     std::vector<long long> rowdst(A1row[nsec], 0);
     std::vector<int> rowslot(A1row[nsec], 0);
     for (int q = 0; q < nsec; ++q)
       for (int t : bysrc[q]) {
-        int d = tasks[t].dst;
+        int d = tdst[t];
         for (int i = 0; i < m[d]; ++i) {
           long long r = A1row[q] + rowin1[t] + i;
           rowdst[r] = stoff[d] + (long long)i * ld2[d] + offk[t];
@@ -616,8 +670,8 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
       }
     long long* dRowdst;
     int* dRowslot;
-    if ((rc = h->alloc(&dRowdst, rowdst.size() * 8))) return bail(rc);
-    if ((rc = h->alloc(&dRowslot, rowslot.size() * 4))) return bail(rc);
+    if ((rc = this->alloc(&dRowdst, rowdst.size() * 8))) return rc;
+    if ((rc = this->alloc(&dRowslot, rowslot.size() * 4))) return rc;
     OZ_CU(cudaMemcpy(dRowdst, rowdst.data(), rowdst.size() * 8, cudaMemcpyHostToDevice));
     OZ_CU(cudaMemcpy(dRowslot, rowslot.data(), rowslot.size() * 4, cudaMemcpyHostToDevice));
 
@@ -627,18 +681,18 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
     for (int q = 0; q < nsec; ++q) {
       if (!bysrc[q].empty()) {
         GemmProblem P{};
-        P.A = h->dA1 + A1off[q]; P.B = h->dB1 + B1off[q]; P.ea = eA1 + A1row[q]; P.eb = h->eB1 + B1row[q];
+        P.A = this->dA1 + A1off[q]; P.B = this->dB1 + B1off[q]; P.ea = eA1 + A1row[q]; P.eb = this->eB1 + B1row[q];
         P.M = rows1[q]; P.N = n[q]; P.nkb = nkb1[q]; P.SA = S; P.SB = S; P.s = s;
-        P.mode = oz::OUT_ROWTABLE; P.C = h->dStage; P.ldc = 0;
-        P.rowdst = dRowdst + A1row[q]; P.rowslot = dRowslot + A1row[q]; P.rowmax = h->mA2;
+        P.mode = oz::OUT_ROWTABLE; P.C = this->dStage; P.ldc = 0;
+        P.rowdst = dRowdst + A1row[q]; P.rowslot = dRowslot + A1row[q]; P.rowmax = this->mA2;
         P.alpha = 1.0; P.beta = 0.0;
         p1.push_back(P);
       }
       if (!bydst[q].empty()) {
         GemmProblem P{};
-        P.A = h->dA2 + A2off[q]; P.B = h->dB2 + B2off[q]; P.ea = h->eA2 + A2row[q]; P.eb = eB2 + B2row[q];
+        P.A = this->dA2 + A2off[q]; P.B = this->dB2 + B2off[q]; P.ea = this->eA2 + A2row[q]; P.eb = eB2 + B2row[q];
         P.M = m[q]; P.N = n[q]; P.nkb = nkb2[q]; P.SA = S; P.SB = S; P.s = s;
-        P.mode = oz::OUT_DENSE; P.C = h->dY + h->psioff[q]; P.ldc = n[q];
+        P.mode = oz::OUT_DENSE; P.C = this->dY + this->psioff[q]; P.ldc = n[q];
         P.alpha = 1.0; P.beta = 0.0;
         p2.push_back(P);
       }
@@ -656,16 +710,16 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
       return tl;
     };
     std::vector<GemmTile> t1 = make_tiles(p1), t2 = make_tiles(p2);
-    h->nt1 = (int)t1.size();
-    h->nt2 = (int)t2.size();
-    if ((rc = h->alloc(&h->dP1, std::max<size_t>(1, p1.size()) * sizeof(GemmProblem)))) return bail(rc);
-    if ((rc = h->alloc(&h->dP2, std::max<size_t>(1, p2.size()) * sizeof(GemmProblem)))) return bail(rc);
-    if ((rc = h->alloc(&h->dT1, std::max<size_t>(1, t1.size()) * sizeof(GemmTile)))) return bail(rc);
-    if ((rc = h->alloc(&h->dT2, std::max<size_t>(1, t2.size()) * sizeof(GemmTile)))) return bail(rc);
-    if (!p1.empty()) OZ_CU(cudaMemcpy(h->dP1, p1.data(), p1.size() * sizeof(GemmProblem), cudaMemcpyHostToDevice));
-    if (!p2.empty()) OZ_CU(cudaMemcpy(h->dP2, p2.data(), p2.size() * sizeof(GemmProblem), cudaMemcpyHostToDevice));
-    if (!t1.empty()) OZ_CU(cudaMemcpy(h->dT1, t1.data(), t1.size() * sizeof(GemmTile), cudaMemcpyHostToDevice));
-    if (!t2.empty()) OZ_CU(cudaMemcpy(h->dT2, t2.data(), t2.size() * sizeof(GemmTile), cudaMemcpyHostToDevice));
+    this->nt1 = (int)t1.size();
+    this->nt2 = (int)t2.size();
+    if ((rc = this->alloc(&this->dP1, std::max<size_t>(1, p1.size()) * sizeof(GemmProblem)))) return rc;
+    if ((rc = this->alloc(&this->dP2, std::max<size_t>(1, p2.size()) * sizeof(GemmProblem)))) return rc;
+    if ((rc = this->alloc(&this->dT1, std::max<size_t>(1, t1.size()) * sizeof(GemmTile)))) return rc;
+    if ((rc = this->alloc(&this->dT2, std::max<size_t>(1, t2.size()) * sizeof(GemmTile)))) return rc;
+    if (!p1.empty()) OZ_CU(cudaMemcpy(this->dP1, p1.data(), p1.size() * sizeof(GemmProblem), cudaMemcpyHostToDevice));
+    if (!p2.empty()) OZ_CU(cudaMemcpy(this->dP2, p2.data(), p2.size() * sizeof(GemmProblem), cudaMemcpyHostToDevice));
+    if (!t1.empty()) OZ_CU(cudaMemcpy(this->dT1, t1.data(), t1.size() * sizeof(GemmTile), cudaMemcpyHostToDevice));
+    if (!t2.empty()) OZ_CU(cudaMemcpy(this->dT2, t2.data(), t2.size() * sizeof(GemmTile), cudaMemcpyHostToDevice));
 
     // ---- per-product slicing segments: psi (B of stage 1) and the concatenated T (A of stage 2)
     std::vector<SliceSeg> sp, sa;
@@ -673,10 +727,10 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
     for (int q = 0; q < nsec; ++q) {
       if (bysrc[q].empty()) continue;
       SliceSeg g{};
-      g.src = h->dPsi + h->psioff[q]; g.ld = n[q]; g.rows = n[q]; g.cols = m[q]; g.prows = g.rows; g.pcols = g.cols;
+      g.src = this->dPsi + this->psioff[q]; g.ld = n[q]; g.rows = n[q]; g.cols = m[q]; g.prows = g.rows; g.pcols = g.cols;
       g.r0 = 0; g.k0 = 0; g.trans = 1; g.S = S; g.scale = 1.0;
-      g.dst = h->dB1 + B1off[q]; g.TR = oz::BN; g.nkb = nkb1[q];
-      g.rowmax = h->mB1 + B1row[q]; g.rowexp = h->eB1 + B1row[q];
+      g.dst = this->dB1 + B1off[q]; g.TR = oz::BN; g.nkb = nkb1[q];
+      g.rowmax = this->mB1 + B1row[q]; g.rowexp = this->eB1 + B1row[q];
       g.unit0 = pd; g.unit0m = pm;
       pd += oz::digit_units(g.prows, g.pcols);
       pm += oz::rowmax_units(g.rows, g.cols);
@@ -685,43 +739,43 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
     for (int q = 0; q < nsec; ++q) {
       if (bydst[q].empty()) continue;
       SliceSeg g{};
-      g.src = h->dStage + stoff[q]; g.ld = ld2[q]; g.rows = m[q]; g.cols = ld2[q]; g.prows = g.rows;
+      g.src = this->dStage + stoff[q]; g.ld = ld2[q]; g.rows = m[q]; g.cols = ld2[q]; g.prows = g.rows;
       g.pcols = g.cols; g.r0 = 0; g.k0 = 0; g.trans = 0; g.S = S; g.scale = 1.0;
-      g.dst = h->dA2 + A2off[q]; g.TR = oz::TILE_M; g.nkb = nkb2[q];
-      g.rowmax = h->mA2 + A2row[q]; g.rowexp = h->eA2 + A2row[q];
+      g.dst = this->dA2 + A2off[q]; g.TR = oz::TILE_M; g.nkb = nkb2[q];
+      g.rowmax = this->mA2 + A2row[q]; g.rowexp = this->eA2 + A2row[q];
       g.unit0 = ad; g.unit0m = 0;
       ad += oz::digit_units(g.prows, g.pcols);
       sa.push_back(g);
     }
-    h->nsegPsi = (int)sp.size();
-    h->nsegA2 = (int)sa.size();
-    h->uPsiM = pm;
-    h->uPsiD = pd;
-    h->uA2D = ad;
-    if ((rc = h->alloc(&h->dSegPsi, std::max<size_t>(1, sp.size()) * sizeof(SliceSeg)))) return bail(rc);
-    if ((rc = h->alloc(&h->dSegA2, std::max<size_t>(1, sa.size()) * sizeof(SliceSeg)))) return bail(rc);
-    if (!sp.empty()) OZ_CU(cudaMemcpy(h->dSegPsi, sp.data(), sp.size() * sizeof(SliceSeg), cudaMemcpyHostToDevice));
-    if (!sa.empty()) OZ_CU(cudaMemcpy(h->dSegA2, sa.data(), sa.size() * sizeof(SliceSeg), cudaMemcpyHostToDevice));
+    this->nsegPsi = (int)sp.size();
+    this->nsegA2 = (int)sa.size();
+    this->uPsiM = pm;
+    this->uPsiD = pd;
+    this->uA2D = ad;
+    if ((rc = this->alloc(&this->dSegPsi, std::max<size_t>(1, sp.size()) * sizeof(SliceSeg)))) return rc;
+    if ((rc = this->alloc(&this->dSegA2, std::max<size_t>(1, sa.size()) * sizeof(SliceSeg)))) return rc;
+    if (!sp.empty()) OZ_CU(cudaMemcpy(this->dSegPsi, sp.data(), sp.size() * sizeof(SliceSeg), cudaMemcpyHostToDevice));
+    if (!sa.empty()) OZ_CU(cudaMemcpy(this->dSegA2, sa.data(), sa.size() * sizeof(SliceSeg), cudaMemcpyHostToDevice));
+  
   }
-
   // ---- CUDA graph of one product (psi and y are the handle's own buffers)
-  OZ_CU(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  OZ_CU(cudaStreamCreateWithFlags(&this->cap, cudaStreamNonBlocking));
   if (mode == OZ_MODE_EAGER) {
     // warm launch outside capture sets kernel attributes once (on a zero psi: no stale NaN patterns)
-    OZ_CU(cudaMemset(h->dPsi, 0, (size_t)h->dim * 8));
-    if ((rc = h->enqueue(h->cap))) return bail(rc);
-    OZ_CU(cudaStreamSynchronize(h->cap));
+    OZ_CU(cudaMemset(this->dPsi, 0, (size_t)this->dim * 8));
+    if ((rc = this->enqueue(this->cap))) return rc;
+    OZ_CU(cudaStreamSynchronize(this->cap));
     cudaGraph_t g;
-    OZ_CU(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-    rc = h->enqueue(h->cap);
-    cudaError_t e = cudaStreamEndCapture(h->cap, &g);
-    if (rc) return bail(rc);
-    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamEndCapture"));
-    e = cudaGraphInstantiate(&h->exec, g, 0);
+    OZ_CU(cudaStreamBeginCapture(this->cap, cudaStreamCaptureModeThreadLocal));
+    rc = this->enqueue(this->cap, true);
+    cudaError_t e = cudaStreamEndCapture(this->cap, &g);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&this->exec, g, 0);
     cudaGraphDestroy(g);
-    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaGraphInstantiate"));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
   }
-  *out = h;
+  prepared = true;
   return OZ_OK;
 }
 
@@ -731,6 +785,8 @@ extern "C" int oz_heff_destroy(oz_heff* h) {
   cudaDeviceSynchronize();
   if (h->exec) cudaGraphExecDestroy(h->exec);
   if (h->cap) cudaStreamDestroy(h->cap);
+  for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);
   delete h;
   return OZ_OK;
@@ -741,6 +797,7 @@ extern "C" int heff_apply(oz_heff* h, const double* psi, double* y, oz_stream_t 
   if (!psi || !y) return fail(OZ_EINVAL, "null vector");
   if (psi == y) return fail(OZ_EINVAL, "y must not alias psi");
   cudaStream_t st = (cudaStream_t)stream;
+  if (int rc = h->prepare()) return rc;
   OZ_CU(cudaMemcpyAsync(h->dPsi, psi, (size_t)h->dim * 8, cudaMemcpyDeviceToDevice, st));
   if (h->exec) {
     OZ_CU(cudaGraphLaunch(h->exec, st));
@@ -748,6 +805,29 @@ extern "C" int heff_apply(oz_heff* h, const double* psi, double* y, oz_stream_t 
     return rc;
   }
   OZ_CU(cudaMemcpyAsync(y, h->dY, (size_t)h->dim * 8, cudaMemcpyDeviceToDevice, st));
+  return OZ_OK;
+}
+
+extern "C" int heff_apply_host(oz_heff* h, const double* psi_host, double* y_host, oz_stream_t stream) {
+  if (!h) return fail(OZ_EINVAL, "handle is null");
+  if (!psi_host || !y_host) return fail(OZ_EINVAL, "null vector");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (int rc = h->prepare()) return rc;
+  OZ_CU(cudaMemcpyAsync(h->dPsi, psi_host, (size_t)h->dim * 8, cudaMemcpyHostToDevice, st));
+  if (h->exec) {
+    OZ_CU(cudaGraphLaunch(h->exec, st));
+  } else if (int rc = h->enqueue(st)) {
+    return rc;
+  }
+  OZ_CU(cudaMemcpyAsync(y_host, h->dY, (size_t)h->dim * 8, cudaMemcpyDeviceToHost, st));
+  return OZ_OK;
+}
+
+extern "C" int oz_heff_stage_times(oz_heff* h, float* ms) {
+  if (!h || !ms) return fail(OZ_EINVAL, "null argument");
+  if (h->mode != OZ_MODE_EAGER) return fail(OZ_EINVAL, "stage times exist for the emulated path only");
+  OZ_CU(cudaEventSynchronize(h->ev[4]));
+  for (int i = 0; i < 4; ++i) OZ_CU(cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]));
   return OZ_OK;
 }
 

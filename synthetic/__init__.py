@@ -73,34 +73,42 @@ def _key(seed: int, stream: int) -> int:
     return _s64(z ^ (z >> 31))
 
 
-def _bits(seed: int, stream: int, n: int, device, lane: int = 0) -> torch.Tensor:
-    ctr = torch.arange(n, dtype=torch.int64, device=device) * 8 + lane
-    return _splitmix(ctr ^ _key(seed, stream))
+# Element idx of the stream (seed, stream) draws lane l from splitmix64((8 idx + l) ^ key(seed, stream)).
+def _lanes(idx: torch.Tensor, key, lane: int) -> torch.Tensor:
+    return _splitmix((idx * 8 + lane) ^ key)
+
+
+def _u01(bits: torch.Tensor) -> torch.Tensor:
+    return _srl(bits, 11).to(torch.float64) * (2.0 ** -53)
+
+
+def _values(idx: torch.Tensor, key, spread: bool) -> torch.Tensor:
+    s = _u01(_lanes(idx, key, 0))
+    s = s + _u01(_lanes(idx, key, 1))
+    s = s + _u01(_lanes(idx, key, 2))
+    s = s + _u01(_lanes(idx, key, 3))
+    v = (s - 2.0) * math.sqrt(3.0)
+    if spread:
+        j = _srl(_lanes(idx, key, 4), 11) % 20  # uniform on 0..19 up to 2^-48
+        u = _u01(_lanes(idx, key, 5))
+        v = v * torch.ldexp(1.0 + u, -j.to(torch.int32))
+    return v
 
 
 def uniform01(seed: int, stream: int, n: int, device="cpu", lane: int = 0) -> torch.Tensor:
     """n uniforms on [0,1), k*2^-53 with k the top 53 hash bits (exact)."""
-    return _srl(_bits(seed, stream, n, device, lane), 11).to(torch.float64) * (2.0 ** -53)
+    return _u01(_lanes(torch.arange(n, dtype=torch.int64, device=device), _key(seed, stream), lane))
 
 
 def normal(seed: int, stream: int, n: int, device="cpu") -> torch.Tensor:
     """Unit-variance Irwin-Hall(4) stand-in for N(0,1), bit-reproducible across devices."""
-    s = uniform01(seed, stream, n, device, 0)
-    s = s + uniform01(seed, stream, n, device, 1)
-    s = s + uniform01(seed, stream, n, device, 2)
-    s = s + uniform01(seed, stream, n, device, 3)
-    return (s - 2.0) * math.sqrt(3.0)
+    return _values(torch.arange(n, dtype=torch.int64, device=device), _key(seed, stream), False)
 
 
 def block_values(seed: int, stream: int, rows: int, cols: int, spread: bool, device="cpu") -> torch.Tensor:
     """A rows x cols float64 block; ``spread`` applies the six-decade exponent spread."""
-    n = rows * cols
-    v = normal(seed, stream, n, device)
-    if spread:
-        j = _srl(_bits(seed, stream, n, device, 4), 11) % 20  # uniform on 0..19 up to 2^-48
-        u = uniform01(seed, stream, n, device, 5)
-        v = v * torch.ldexp(1.0 + u, -j.to(torch.int32))
-    return v.reshape(rows, cols)
+    idx = torch.arange(rows * cols, dtype=torch.int64, device=device)
+    return _values(idx, _key(seed, stream), spread).reshape(rows, cols)
 
 
 # --------------------------------------------------------------------------------------------
@@ -253,6 +261,51 @@ def gen_task_blocks(st: HeffStructure, t: int, value_seed: int = 2, device="cpu"
     if odd:
         Lb, Rb = Lb.T.contiguous(), Rb.T.contiguous()
     return Lb, Rb
+
+
+def gen_all_task_blocks(st: HeffStructure, value_seed: int = 2, device="cuda", chunk: int = 1 << 27):
+    """All (L_t, R_t) blocks, generated in large batches (bit-identical to gen_task_blocks).
+
+    Returns (Lbuf, Rbuf, Loff, Roff): flat float64 buffers and per-task element offsets; task t's
+    L block is Lbuf[Loff[t]:Loff[t]+m[dst]*m[src]].view(m[dst], m[src]) (likewise R with n)."""
+    t = st.tasks
+    mdst, msrc = st.m[t[:, 2]].astype(np.int64), st.m[t[:, 1]].astype(np.int64)
+    ndst, nsrc = st.n[t[:, 2]].astype(np.int64), st.n[t[:, 1]].astype(np.int64)
+    out = []
+    for side, (r, c) in enumerate(((mdst, msrc), (ndst, nsrc))):
+        sizes = r * c
+        off = np.concatenate([[0], np.cumsum(sizes)])
+        buf = torch.empty(int(off[-1]), dtype=torch.float64, device=device)
+        owners = np.nonzero(t[:, 0] % 2 == 0)[0]
+        keys = np.array([_key(value_seed, _task_stream(st, int(i), side)) for i in owners], dtype=np.int64)
+        # batches of owner tasks with about `chunk` elements each
+        start = 0
+        while start < len(owners):
+            tot, end = 0, start
+            while end < len(owners) and (tot == 0 or tot + sizes[owners[end]] <= chunk):
+                tot += int(sizes[owners[end]])
+                end += 1
+            sel = owners[start:end]
+            sz = torch.as_tensor(sizes[sel], device=device)
+            kk = torch.as_tensor(keys[start:end], device=device)
+            which = torch.repeat_interleave(torch.arange(len(sel), device=device), sz)
+            first = torch.cumsum(sz, 0) - sz
+            local = torch.arange(tot, dtype=torch.int64, device=device) - first[which]
+            vals = _values(local, kk[which], st.spread)
+            pos = 0
+            for i, ti in enumerate(sel):
+                n_ = int(sizes[ti])
+                buf[off[ti]:off[ti] + n_].copy_(vals[pos:pos + n_])
+                pos += n_
+            del vals, local, which
+            start = end
+        # partners are transposes of their owner's block
+        for ti in np.nonzero(t[:, 0] % 2 == 1)[0]:
+            p = int(st.partner[ti])
+            src = buf[off[p]:off[p] + sizes[p]].view(int(r[p]), int(c[p]))
+            buf[off[ti]:off[ti] + sizes[ti]].view(int(r[ti]), int(c[ti])).copy_(src.T)
+        out += [buf, off]
+    return out[0], out[2], out[1], out[3]
 
 
 def gen_psi(st: HeffStructure, seed: int = 3, device="cpu") -> torch.Tensor:
