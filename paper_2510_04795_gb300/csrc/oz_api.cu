@@ -35,6 +35,9 @@ int cuda_fail(cudaError_t e, const char* where) {
   } while (0)
 
 inline long long cdiv(long long a, long long b) { return (a + b - 1) / b; }
+// Longest reduction one product accepts: the epilogue's two 64-bit partial sums stay exact while
+// every diagonal has fewer than 2^13 accumulator groups of GROUP_TERMS products.
+constexpr long long OZ_MAX_K = 1ll << 20;
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 int check_prec(const oz_prec* p, int* S, int* s, int* mode) {
@@ -204,6 +207,7 @@ extern "C" int ozaki_gemm(oz_ctx* c, int m, int n, int k, double alpha, const do
   if (m < 0 || n < 0 || k < 0) return fail(OZ_EINVAL, "negative size");
   if (lda < std::max(k, 1) || ldb < std::max(n, 1) || ldc < std::max(n, 1)) return fail(OZ_EINVAL, "leading dimension too small");
   if (m == 0 || n == 0) return OZ_OK;
+  if (k > OZ_MAX_K) return fail(OZ_EINVAL, "k exceeds the exact-accumulation limit (1048576)");
   cudaStream_t st = (cudaStream_t)stream;
   if (k == 0) {
     scale_kernel<<<(unsigned)cdiv((long long)m * n, 256), 256, 0, st>>>(C, m, n, ldc, beta);
@@ -458,6 +462,7 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
       offk[t] = k2;
       k2 += cdiv(n[tasks[t].src], 8) * 8;
     }
+    if (k2 > OZ_MAX_K) return bail(fail(OZ_EINVAL, "a target sector's concatenated reduction exceeds 1048576"));
     nkb2[q] = (int)cdiv(std::max(k2, 1ll), oz::KB);
     ld2[q] = nkb2[q] * oz::KB;
   }

@@ -11,9 +11,10 @@
 
 namespace oz {
 
-// Digit tiles: K-blocks of 32 FP16 digits; "core matrices" of 8 rows x 8 K-elements
+// Digit tiles: K-blocks of KB FP16 digits; "core matrices" of 8 rows x 8 K-elements
 // (128 contiguous bytes) in the no-swizzle K-major canonical layout of tcgen05.mma.
-constexpr int KB = 32;                 // K elements per k-block
+constexpr int KB_SHIFT = 4;
+constexpr int KB = 1 << KB_SHIFT;      // K elements per k-block (one MMA K-step of 16)
 constexpr int KB_CM = KB / 8;          // core matrices along K in one k-block
 constexpr int TILE_M = 128;            // A-operand tile rows (MMA M)
 constexpr int GROUP_TERMS = 1008;      // products per FP32 accumulator group: 1008 * 2^14 < 2^24
@@ -179,7 +180,7 @@ OZ_DEVICE_INLINE unsigned long long round_shift(unsigned long long M, int sh) {
 }
 
 // RN_even(Z * 2^E) as IEEE binary64, Z a signed 128-bit integer.
-OZ_DEVICE_INLINE double int128_to_double(__int128 Z, int E) {
+static __device__ __noinline__ double int128_to_double(__int128 Z, int E) {
   if (Z == 0) return 0.0;
   unsigned long long sign = 0;
   unsigned __int128 a;

@@ -9,7 +9,7 @@
 // integer below 2^24 and the accumulation is exact (checked on the device against int64).
 //
 // One CTA per SM, persistent over a tile list; 10 warps:
-//   warp 0       producer: cp.async.bulk of pre-tiled digit planes into a 2-stage ring
+//   warp 0       producer: cp.async.bulk of pre-tiled digit planes into an NSTAGE ring
 //   warp 1       TMEM owner and single-thread MMA issuer; diagonal g = t+u-2 of the slice grid
 //                accumulates into its own TMEM buffer (BN columns), A reused through the
 //                collector across the u loop; a full buffer is handed to the epilogue ("drain")
@@ -47,7 +47,7 @@ struct MmaCtl {
 
 __device__ __forceinline__ uint32_t bar(const unsigned long long* p) { return smem_u32(p); }
 
-__device__ __forceinline__ void post(Shared& sh, MmaCtl& c, uint32_t b, int shift, int flags) {
+__device__ __noinline__ void post(Shared& sh, MmaCtl& c, uint32_t b, int shift, int flags) {
   tc_commit(bar(&sh.accf[b]));
   int slot = c.qseq % QN;
   sh.rec[slot] = make_int4((int)b, shift, flags, 0);
@@ -55,7 +55,7 @@ __device__ __forceinline__ void post(Shared& sh, MmaCtl& c, uint32_t b, int shif
   c.qseq++;
 }
 
-__device__ __forceinline__ uint32_t acquire(Shared& sh, MmaCtl& c, volatile int* abort) {
+__device__ __noinline__ uint32_t acquire(Shared& sh, MmaCtl& c, volatile int* abort) {
   if (c.fresh < NBUF) return (uint32_t)c.fresh++;
   int slot = c.reclaim % QN;
   uint32_t b = (uint32_t)sh.rec[slot].x;
@@ -66,50 +66,59 @@ __device__ __forceinline__ uint32_t acquire(Shared& sh, MmaCtl& c, volatile int*
   return b;
 }
 
+// MMAs of one output tile at slice level S.  Per k-block (one K-step of 16) diagonal g = t + u
+// (0-based) receives g + 1 slice-pair products of 16 terms each; before the k-block, every diagonal
+// whose group could not absorb them is drained (its buffer handed to the epilogue and replaced), so
+// the MMA sequence itself is branch-free.  First groups are shortened by a per-diagonal offset so
+// that the drains of different diagonals fall into different k-blocks.
 template <int S>
 __device__ void mma_tile(Shared& sh, MmaCtl& c, uint32_t tmem, uint32_t stage0, int nkb, volatile int* abort) {
   constexpr uint32_t IDESC = idesc_f16(TILE_M, BN);
   uint32_t buf[S];
-  int cnt[S];
+  int room[S];
 #pragma unroll
   for (int g = 0; g < S; ++g) {
     buf[g] = acquire(sh, c, abort);
-    cnt[g] = 0;
+    const int per = 16 * (g + 1);
+    const int period = GROUP_TERMS / per;              // k-blocks per full group
+    room[g] = GROUP_TERMS - per * ((g * period) / S);   // staggered first group
   }
+  uint32_t fresh = (1u << S) - 1u;  // diagonals whose current buffer has not been written yet
   for (int kb = 0; kb < nkb; ++kb) {
-    int stg = (int)(c.it % NSTAGE);
-    uint32_t par = (uint32_t)((c.it / NSTAGE) & 1);
+    const int stg = (int)(c.it % NSTAGE);
+    const uint32_t par = (uint32_t)((c.it / NSTAGE) & 1);
+#pragma unroll
+    for (int g = 0; g < S; ++g) {
+      if (room[g] < 16 * (g + 1)) {
+        post(sh, c, buf[g], 8 * (S - 1 - g), 0);
+        buf[g] = acquire(sh, c, abort);
+        room[g] = GROUP_TERMS;
+        fresh |= 1u << g;
+      }
+      room[g] -= 16 * (g + 1);
+    }
     if (!mbar_wait(bar(&sh.full[stg]), par, abort)) return;
-    tc_fence_after();
-    uint32_t aaddr = stage0 + stg * STAGE_BYTES;
-    uint32_t baddr = aaddr + MAX_LEVEL * A_TILE_BYTES;
-    uint64_t ad0 = smem_desc(aaddr, 128, 128 * KB_CM);
-    uint64_t bd0 = smem_desc(baddr, 128, 128 * KB_CM);
+    const uint32_t aaddr = stage0 + stg * STAGE_BYTES;
+    const uint64_t ad0 = smem_desc(aaddr, 128, 128 * KB_CM);
+    const uint64_t bd0 = smem_desc(aaddr + MAX_LEVEL * A_TILE_BYTES, 128, 128 * KB_CM);
 #pragma unroll
-    for (int ks = 0; ks < 2; ++ks) {
+    for (int t = 0; t < S; ++t) {
+      const uint64_t ad = ad0 + (uint64_t)((t * A_TILE_BYTES) >> 4);
 #pragma unroll
-      for (int t = 0; t < S; ++t) {
-        const uint64_t ad = ad0 + (uint64_t)((t * A_TILE_BYTES + ks * 256) >> 4);
-#pragma unroll
-        for (int u = 0; u < S - t; ++u) {
-          const int g = t + u;
-          if (cnt[g] + 16 > GROUP_TERMS) {
-            post(sh, c, buf[g], 8 * (S - 1 - g), 0);
-            buf[g] = acquire(sh, c, abort);
-            cnt[g] = 0;
-          }
-          const uint64_t bd = bd0 + (uint64_t)((u * B_TILE_BYTES + ks * 256) >> 4);
-          const uint32_t d = tmem + buf[g] * BN;
-          const uint32_t acc = cnt[g] > 0 ? 1u : 0u;
-          const int nu = S - t;
-          if (nu == 1) mma_f16<0>(d, ad, bd, IDESC, acc);
-          else if (u == 0) mma_f16<1>(d, ad, bd, IDESC, acc);
-          else if (u == nu - 1) mma_f16<3>(d, ad, bd, IDESC, acc);
-          else mma_f16<2>(d, ad, bd, IDESC, acc);
-          cnt[g] += 16;
-        }
+      for (int u = 0; u < S - t; ++u) {
+        const int g = t + u;
+        const uint64_t bd = bd0 + (uint64_t)((u * B_TILE_BYTES) >> 4);
+        const uint32_t d = tmem + buf[g] * BN;
+        // the first product of a k-block into diagonal g is the one with t = 0
+        const uint32_t acc = (t == 0) ? (((fresh >> g) & 1u) ^ 1u) : 1u;
+        const int nu = S - t;
+        if (nu == 1) mma_f16<0>(d, ad, bd, IDESC, acc);
+        else if (u == 0) mma_f16<1>(d, ad, bd, IDESC, acc);
+        else if (u == nu - 1) mma_f16<3>(d, ad, bd, IDESC, acc);
+        else mma_f16<2>(d, ad, bd, IDESC, acc);
       }
     }
+    fresh = 0u;
     tc_commit(bar(&sh.empty[stg]));
     c.it++;
   }
@@ -226,11 +235,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const GemmProblem* P;
       int mb, nb;
       tile_of(tiles, probs, single, idx, P, mb, nb);
-      unsigned long long zlo[32];
-      long long zhi[32];
+      // exact running sum Z = zhi * 2^32 + zlo; drains with shift < 32 go to zlo, the others to zhi
+      // (each part stays below 2^62 in magnitude for levels <= 8 and fewer than 2^14 groups per diagonal)
+      long long zlo[32], zhi[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
-        zlo[j] = 0ull;
+        zlo[j] = 0ll;
         zhi[j] = 0ll;
       }
       bool ok = true;
@@ -250,52 +260,57 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(bar(&sh.acce[b]));
         const int shl = r.y;
+        if (shl < 32) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const long long q = (long long)__float2int_rn(__uint_as_float(v[j]));
-          const unsigned long long lo = (unsigned long long)q << shl;
-          const long long hi = shl ? (q >> (64 - shl)) : (q >> 63);
-          asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(zlo[j]), "+l"(zhi[j]) : "l"(lo), "l"(hi));
+          for (int j = 0; j < 32; ++j) zlo[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << shl;
+        } else {
+          const int sh2 = shl - 32;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) zhi[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << sh2;
         }
         ++eseq;
         if (r.z & 1) break;
       }
       if (!ok) break;
       // ---- one rounding to FP64, scaling, store
+      const int M = P->M, N = P->N, s = P->s, mode = P->mode;
       const int row = mb * TILE_M + lq * 32 + lane;
-      if (row < P->M) {
-        const int s = P->s;
-        const int ea = P->ea[row] - 8 * s - 6;
+      if (row < M) {
+        const int* __restrict__ eb = P->eb;
+        const int ea = __ldg(P->ea + row) - 8 * s - 6;
         const int col0 = nb * BN + ch * 32;
-        if (P->mode == OUT_DENSE) {
-          double* crow = P->C + (long long)row * P->ldc;
+        const int ncol = min(32, N - col0);
+        if (mode == OUT_DENSE) {
+          double* crow = P->C + (long long)row * P->ldc + col0;
           const double alpha = P->alpha, beta = P->beta;
+          const bool plain = (alpha == 1.0) && (beta == 0.0);
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            const int col = col0 + j;
-            if (col < P->N) {
-              const __int128 Z = ((__int128)zhi[j] << 64) | (__int128)zlo[j];
-              double c = int128_to_double(Z, ea + P->eb[col]);
-              if (alpha != 1.0) c = __dmul_rn(alpha, c);
-              if (beta != 0.0) c = __dadd_rn(c, __dmul_rn(beta, crow[col]));
-              crow[col] = c;
+            if (j < ncol) {
+              const __int128 Z = ((__int128)zhi[j] << 32) + (__int128)zlo[j];
+              double c = int128_to_double(Z, ea + __ldg(eb + col0 + j));
+              if (!plain) {
+                c = __dmul_rn(alpha, c);
+                if (beta != 0.0) c = __dadd_rn(c, __dmul_rn(beta, crow[j]));
+              }
+              crow[j] = c;
             }
           }
         } else {
-          double* crow = P->C + P->rowdst[row];
+          double* crow = P->C + __ldg(P->rowdst + row) + col0;
           unsigned long long mx = 0;
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            const int col = col0 + j;
-            if (col < P->N) {
-              const __int128 Z = ((__int128)zhi[j] << 64) | (__int128)zlo[j];
-              const double c = int128_to_double(Z, ea + P->eb[col]);
-              crow[col] = c;
+            if (j < ncol) {
+              const __int128 Z = ((__int128)zhi[j] << 32) + (__int128)zlo[j];
+              const double c = int128_to_double(Z, ea + __ldg(eb + col0 + j));
+              crow[j] = c;
               const unsigned long long bb = (unsigned long long)__double_as_longlong(c) & 0x7FFFFFFFFFFFFFFFull;
               mx = bb > mx ? bb : mx;
             }
           }
-          if (P->rowmax && mx) atomicMax(P->rowmax + P->rowslot[row], mx);
+          unsigned long long* rmax = P->rowmax;
+          if (rmax && mx) atomicMax(rmax + __ldg(P->rowslot + row), mx);
         }
       }
     }

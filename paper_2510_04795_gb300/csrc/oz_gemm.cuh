@@ -6,7 +6,7 @@ namespace oz {
 
 constexpr int BN = 64;              // output tile columns (MMA N)
 constexpr int NBUF = 512 / BN;      // TMEM accumulator buffers of BN columns
-constexpr int NSTAGE = 2;           // shared-memory pipeline stages
+constexpr int NSTAGE = 4;           // shared-memory pipeline stages
 constexpr int MAX_LEVEL = 8;        // slice levels supported by the BN = 64 kernel (one buffer per diagonal)
 constexpr int QN = 16;              // drain-record ring
 
@@ -19,7 +19,7 @@ struct GemmProblem {
   const __half* B;
   const int* ea;               // per A row exponent
   const int* eb;               // per B^T row (output column) exponent
-  int M, N, nkb;               // sizes, k-blocks of 32
+  int M, N, nkb;               // sizes, k-blocks of KB
   int SA, SB;                  // planes stored per k-block in A / B^T
   int s;                       // slice level (1..MAX_LEVEL)
   int mode;                    // OUT_DENSE or OUT_ROWTABLE

@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) digits_kernel(const SliceSeg* __restrict_
     }
   }
   int K = g.k0 + c * 8;
-  int rt = R / g.TR, rr = R % g.TR, kb = K >> 5, kk = K & 31;
+  int rt = R / g.TR, rr = R % g.TR, kb = K >> KB_SHIFT, kk = K & (KB - 1);
   long long base = (((long long)rt * g.nkb + kb) * g.S) * (long long)(g.TR * KB) + tile_off(rr, kk);
 #pragma unroll
   for (int t = 0; t < S; ++t) {
@@ -159,7 +159,7 @@ __global__ void untile_kernel(const __half* __restrict__ dig, int TR, int nkb, i
   int j = (int)(idx % cols);
   int i = (int)((idx / cols) % rows);
   int t = (int)(idx / ((long long)rows * cols));
-  int rt = i / TR, rr = i % TR, kb = j >> 5, kk = j & 31;
+  int rt = i / TR, rr = i % TR, kb = j >> KB_SHIFT, kk = j & (KB - 1);
   long long off = (((long long)rt * nkb + kb) * S + t) * (long long)(TR * KB) + tile_off(rr, kk);
   out[idx] = (int8_t)__half2int_rn(dig[off]);
 }
