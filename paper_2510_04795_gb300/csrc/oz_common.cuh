@@ -225,4 +225,44 @@ static __device__ __noinline__ double int128_to_double(__int128 Z, int E) {
   return __longlong_as_double((long long)bits);
 }
 
+// RN_even((zhi * 2^32 + zlo) * 2^E): fast path for results in the normal range (64-bit integer
+// operations only), general path otherwise.
+OZ_DEVICE_INLINE double split_to_double(long long zhi, long long zlo, int E) {
+  const unsigned long long L1 = (unsigned long long)zhi << 32;
+  unsigned long long l = L1 + (unsigned long long)zlo;
+  unsigned long long h = (unsigned long long)((zhi >> 32) + (zlo >> 63) + (l < L1 ? 1ll : 0ll));
+  const unsigned long long sign = h & 0x8000000000000000ull;
+  if (sign) {
+    l = ~l + 1ull;
+    h = ~h + (l == 0ull ? 1ull : 0ull);
+  }
+  if ((h | l) == 0ull) return 0.0;
+  int nb;
+  unsigned long long top;
+  bool sticky;
+  if (h) {
+    const int lz = __clzll((long long)h);
+    nb = 128 - lz;
+    top = lz ? ((h << lz) | (l >> (64 - lz))) : h;
+    sticky = (lz ? (l << lz) : l) != 0ull;
+  } else {
+    const int lz = __clzll((long long)l);
+    nb = 64 - lz;
+    top = l << lz;
+    sticky = false;
+  }
+  int e2 = nb - 1 + E;
+  if (e2 < -1022 || e2 > 1022) return int128_to_double(((__int128)zhi << 32) + (__int128)zlo, E);
+  unsigned long long m = top >> 11;
+  const unsigned long long g = top & 0x7FFull;
+  if (g > 0x400ull || (g == 0x400ull && (sticky || (m & 1ull)))) {
+    m += 1ull;
+    if (m >> 53) {
+      m >>= 1;
+      e2 += 1;
+    }
+  }
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(e2 + 1023) << 52) | (m & ((1ull << 52) - 1))));
+}
+
 }  // namespace oz

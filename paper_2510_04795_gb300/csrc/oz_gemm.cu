@@ -10,14 +10,18 @@
 //
 // One CTA per SM, persistent over a tile list; 10 warps:
 //   warp 0       producer: cp.async.bulk of pre-tiled digit planes into an NSTAGE ring
-//   warp 1       TMEM owner and single-thread MMA issuer; diagonal g = t+u-2 of the slice grid
-//                accumulates into its own TMEM buffer (BN columns), A reused through the
-//                collector across the u loop; a full buffer is handed to the epilogue ("drain")
-//                and replaced by a free one, so the MMA never waits on the epilogue while a
-//                spare buffer exists
-//   warps 2..9   epilogue: exact 128-bit running sums Z += q * 256^(s-1-g) per output element,
-//                then one round-to-nearest-even to FP64 scaled by 2^(ea+eb-8s-6), alpha/beta,
-//                store (and for the row-table mode a per-row |max| for the next slicing).
+//   warp 1       TMEM owner and single-thread MMA issuer; diagonal g = t+u (0-based) of the slice
+//                grid accumulates into its own TMEM buffer (BN columns), A reused through the
+//                collector across the u loop; a buffer whose group is full is handed to the
+//                epilogue ("drain": one tcgen05.commit) and replaced by a free one
+//   warps 2..9   epilogue: replays the same deterministic drain/buffer schedule, reads each
+//                drained buffer, adds q * 256^(s-1-g) into exact running sums per output element,
+//                then rounds once to FP64 scaled by 2^(ea+eb-8s-6), applies alpha/beta, stores
+//                (and for the row-table mode records a per-row |max| for the next slicing).
+// The drain schedule: diagonal g takes p = 16(g+1) products per k-block; its groups hold
+// floor(GROUP_TERMS/p) k-blocks (the first group of long tiles is shortened per diagonal so that the
+// drains of different diagonals do not coincide).  The first k-block of a tile is issued diagonal by
+// diagonal, heaviest first, so that it starts while the previous tile's last buffers are drained.
 // Every wait is bounded; a timeout sets *err and all roles leave their loops.
 #include "oz_gemm.cuh"
 
@@ -27,77 +31,114 @@ constexpr int A_TILE_BYTES = TILE_M * KB * 2;   // 8 KB per plane
 constexpr int B_TILE_BYTES = BN * KB * 2;       // 4 KB per plane
 constexpr int STAGE_BYTES = MAX_LEVEL * (A_TILE_BYTES + B_TILE_BYTES);
 constexpr int NTHREADS = 320;
+constexpr int OUT_LD = 9;                             // staging row stride (doubles), breaks bank conflicts
+constexpr int OUT_STAGE_BYTES = 8 * 32 * OUT_LD * 8;  // 8 epilogue warps x 32 rows x 8 columns
 
 struct Shared {
-  unsigned long long full[NSTAGE], empty[NSTAGE], accf[NBUF], acce[NBUF], qfull[QN], fin;
-  int4 rec[QN];
+  unsigned long long full[NSTAGE], empty[NSTAGE], accf[NBUF], acce[NBUF], fin;
   uint32_t tmem;
   int abort;
 };
 
-size_t gemm_smem_bytes() { return (size_t)NSTAGE * STAGE_BYTES + sizeof(Shared) + 1024; }
-
-struct MmaCtl {
-  long long it;      // k-block iterations issued (ring position)
-  int fresh;         // buffers never used yet
-  int qseq;          // drain records posted
-  int reclaim;       // next record whose buffer is reused
-  uint32_t acce_par; // per buffer parity of the next "drained" wait
-};
+size_t gemm_smem_bytes() { return (size_t)NSTAGE * STAGE_BYTES + OUT_STAGE_BYTES + sizeof(Shared) + 1024; }
 
 __device__ __forceinline__ uint32_t bar(const unsigned long long* p) { return smem_u32(p); }
 
-__device__ __noinline__ void post(Shared& sh, MmaCtl& c, uint32_t b, int shift, int flags) {
-  tc_commit(bar(&sh.accf[b]));
-  int slot = c.qseq % QN;
-  sh.rec[slot] = make_int4((int)b, shift, flags, 0);
-  mbar_arrive(bar(&sh.qfull[slot]));
-  c.qseq++;
-}
+// Deterministic TMEM buffer assignment, replayed identically by the MMA issuer and the epilogue:
+// the n-th acquisition returns buffer n while n < NBUF, afterwards the buffer of post n - NBUF.
+struct BufRing {
+  uint32_t ring;  // buffers of the last 8 posts, 4 bits each
+  int nacq, npost;
+  __device__ __forceinline__ uint32_t next() {
+    const uint32_t b = nacq < NBUF ? (uint32_t)nacq : (ring >> (4 * ((nacq - NBUF) & 7))) & 0xFu;
+    ++nacq;
+    return b;
+  }
+  __device__ __forceinline__ void posted(uint32_t b) {
+    const int j = npost & 7;
+    ring = (ring & ~(0xFu << (4 * j))) | (b << (4 * j));
+    ++npost;
+  }
+};
 
-__device__ __noinline__ uint32_t acquire(Shared& sh, MmaCtl& c, volatile int* abort) {
-  if (c.fresh < NBUF) return (uint32_t)c.fresh++;
-  int slot = c.reclaim % QN;
-  uint32_t b = (uint32_t)sh.rec[slot].x;
-  c.reclaim++;
-  mbar_wait(bar(&sh.acce[b]), (c.acce_par >> b) & 1u, abort);
-  c.acce_par ^= 1u << b;
-  tc_fence_after();
+// k-block of the first drain of diagonal g and the drain period (both in k-blocks)
+__device__ __forceinline__ void drain_plan(int g, int S, bool stagger, int& first, int& period) {
+  const int p = 16 * (g + 1);
+  period = GROUP_TERMS / p;
+  const int room0 = stagger ? GROUP_TERMS - p * ((g * period) / S) : GROUP_TERMS;
+  first = room0 / p;
+}
+__device__ __forceinline__ bool stagger_of(int nkb) { return nkb >= 64; }
+
+struct MmaCtl {
+  long long it;       // k-block iterations issued (ring position)
+  BufRing r;
+  uint32_t acce_par;  // per buffer parity of the next "drained" wait
+};
+
+__device__ __forceinline__ uint32_t acquire(Shared& sh, MmaCtl& c, volatile int* abort) {
+  const bool reused = c.r.nacq >= NBUF;
+  const uint32_t b = c.r.next();
+  if (reused) {
+    mbar_wait(bar(&sh.acce[b]), (c.acce_par >> b) & 1u, abort);
+    c.acce_par ^= 1u << b;
+    tc_fence_after();
+  }
   return b;
 }
+__device__ __forceinline__ void post(Shared& sh, MmaCtl& c, uint32_t b) {
+  tc_commit(bar(&sh.accf[b]));
+  c.r.posted(b);
+}
 
-// MMAs of one output tile at slice level S.  Per k-block (one K-step of 16) diagonal g = t + u
-// (0-based) receives g + 1 slice-pair products of 16 terms each; before the k-block, every diagonal
-// whose group could not absorb them is drained (its buffer handed to the epilogue and replaced), so
-// the MMA sequence itself is branch-free.  First groups are shortened by a per-diagonal offset so
-// that the drains of different diagonals fall into different k-blocks.
 template <int S>
 __device__ void mma_tile(Shared& sh, MmaCtl& c, uint32_t tmem, uint32_t stage0, int nkb, volatile int* abort) {
   constexpr uint32_t IDESC = idesc_f16(TILE_M, BN);
   uint32_t buf[S];
-  int room[S];
+  int nxt[S], per[S];
+  const bool stag = stagger_of(nkb);
+  int nmin = 1 << 30;
 #pragma unroll
   for (int g = 0; g < S; ++g) {
-    buf[g] = acquire(sh, c, abort);
-    const int per = 16 * (g + 1);
-    const int period = GROUP_TERMS / per;              // k-blocks per full group
-    room[g] = GROUP_TERMS - per * ((g * period) / S);   // staggered first group
+    drain_plan(g, S, stag, nxt[g], per[g]);
+    nmin = min(nmin, nxt[g]);
   }
-  uint32_t fresh = (1u << S) - 1u;  // diagonals whose current buffer has not been written yet
-  for (int kb = 0; kb < nkb; ++kb) {
+  // ---- k-block 0: diagonal by diagonal (heaviest first), each as soon as its buffer is free
+  {
     const int stg = (int)(c.it % NSTAGE);
-    const uint32_t par = (uint32_t)((c.it / NSTAGE) & 1);
+    if (!mbar_wait(bar(&sh.full[stg]), (uint32_t)((c.it / NSTAGE) & 1), abort)) return;
+    const uint32_t aaddr = stage0 + stg * STAGE_BYTES;
+    const uint64_t ad0 = smem_desc(aaddr, 128, 128 * KB_CM);
+    const uint64_t bd0 = smem_desc(aaddr + MAX_LEVEL * A_TILE_BYTES, 128, 128 * KB_CM);
 #pragma unroll
-    for (int g = 0; g < S; ++g) {
-      if (room[g] < 16 * (g + 1)) {
-        post(sh, c, buf[g], 8 * (S - 1 - g), 0);
-        buf[g] = acquire(sh, c, abort);
-        room[g] = GROUP_TERMS;
-        fresh |= 1u << g;
-      }
-      room[g] -= 16 * (g + 1);
+    for (int g = S - 1; g >= 0; --g) {
+      buf[g] = acquire(sh, c, abort);
+      const uint32_t d = tmem + buf[g] * BN;
+#pragma unroll
+      for (int t = 0; t <= g; ++t)
+        mma_f16<0>(d, ad0 + (uint64_t)((t * A_TILE_BYTES) >> 4), bd0 + (uint64_t)(((g - t) * B_TILE_BYTES) >> 4), IDESC,
+                   t > 0 ? 1u : 0u);
     }
-    if (!mbar_wait(bar(&sh.full[stg]), par, abort)) return;
+    tc_commit(bar(&sh.empty[stg]));
+    c.it++;
+  }
+  uint32_t fresh = 0u;  // diagonals whose current buffer has not been written yet
+  for (int kb = 1; kb < nkb; ++kb) {
+    if (kb == nmin) {
+      nmin = 1 << 30;
+#pragma unroll
+      for (int g = 0; g < S; ++g) {
+        if (nxt[g] == kb) {
+          post(sh, c, buf[g]);
+          buf[g] = acquire(sh, c, abort);
+          fresh |= 1u << g;
+          nxt[g] += per[g];
+        }
+        nmin = min(nmin, nxt[g]);
+      }
+    }
+    const int stg = (int)(c.it % NSTAGE);
+    if (!mbar_wait(bar(&sh.full[stg]), (uint32_t)((c.it / NSTAGE) & 1), abort)) return;
     const uint32_t aaddr = stage0 + stg * STAGE_BYTES;
     const uint64_t ad0 = smem_desc(aaddr, 128, 128 * KB_CM);
     const uint64_t bd0 = smem_desc(aaddr + MAX_LEVEL * A_TILE_BYTES, 128, 128 * KB_CM);
@@ -123,7 +164,32 @@ __device__ void mma_tile(Shared& sh, MmaCtl& c, uint32_t tmem, uint32_t stage0, 
     c.it++;
   }
 #pragma unroll
-  for (int g = 0; g < S; ++g) post(sh, c, buf[g], 8 * (S - 1 - g), g == S - 1 ? 1 : 0);
+  for (int g = 0; g < S; ++g) post(sh, c, buf[g]);
+}
+
+// Epilogue side of one drain: wait until the MMAs into buffer b are complete, read this warp's
+// 32 x 32 slice, release the buffer, add q * 2^shl into the exact running sums.
+__device__ __forceinline__ bool drain_into(Shared& sh, uint32_t tmem, int lq, int ch, int lane, uint32_t b, int shl,
+                                           uint32_t& accf_par, volatile int* abort, long long (&zlo)[32],
+                                           long long (&zhi)[32]) {
+  if (!mbar_wait(bar(&sh.accf[b]), (accf_par >> b) & 1u, abort)) return false;
+  accf_par ^= 1u << b;
+  tc_fence_after();
+  uint32_t v[32];
+  tmem_ld32(tmem + ((uint32_t)(lq * 32) << 16) + b * BN + ch * 32, v);
+  tmem_wait_ld();
+  tc_fence_before();
+  __syncwarp();
+  if (lane == 0) mbar_arrive(bar(&sh.acce[b]));
+  if (shl < 32) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) zlo[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << shl;
+  } else {
+    const int sh2 = shl - 32;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) zhi[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << sh2;
+  }
+  return true;
 }
 
 __device__ __forceinline__ void tile_of(const GemmTile* tiles, const GemmProblem* probs, const GemmProblem& single,
@@ -146,7 +212,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const __grid_constant__ GemmProblem single, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  Shared& sh = *reinterpret_cast<Shared*>(smem + NSTAGE * STAGE_BYTES);
+  double* out_stage = reinterpret_cast<double*>(smem + NSTAGE * STAGE_BYTES);
+  Shared& sh = *reinterpret_cast<Shared*>(smem + NSTAGE * STAGE_BYTES + OUT_STAGE_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* abort = &sh.abort;
   const uint32_t stage0 = smem_u32(smem);
@@ -160,7 +227,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(bar(&sh.accf[i]), 1);
       mbar_init(bar(&sh.acce[i]), 8);
     }
-    for (int i = 0; i < QN; ++i) mbar_init(bar(&sh.qfull[i]), 1);
     mbar_init(bar(&sh.fin), 1);
     sh.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -202,7 +268,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      MmaCtl c{0, 0, 0, 0, 0u};
+      MmaCtl c{0, BufRing{0u, 0, 0}, 0u};
       for (int idx = blockIdx.x; idx < ntiles && !*abort; idx += gridDim.x) {
         const GemmProblem* P;
         int mb, nb;
@@ -229,14 +295,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ------------------------------------------------------------------ epilogue
     const int lq = warp & 3;            // TMEM lane quarter this warp may access
     const int ch = (warp - 2) >> 2;     // column half of the BN-wide tile
-    long long eseq = 0;
     uint32_t accf_par = 0;
+    BufRing er{0u, 0, 0};
     for (int idx = blockIdx.x; idx < ntiles && !*abort; idx += gridDim.x) {
       const GemmProblem* P;
       int mb, nb;
       tile_of(tiles, probs, single, idx, P, mb, nb);
       // exact running sum Z = zhi * 2^32 + zlo; drains with shift < 32 go to zlo, the others to zhi
-      // (each part stays below 2^62 in magnitude for levels <= 8 and fewer than 2^14 groups per diagonal)
+      // (each part stays below 2^62 in magnitude for levels <= 8 and fewer than 2^13 groups per diagonal)
       long long zlo[32], zhi[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
@@ -244,75 +310,77 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         zhi[j] = 0ll;
       }
       bool ok = true;
-      while (true) {
-        const int slot = (int)(eseq % QN);
-        if (!mbar_wait(bar(&sh.qfull[slot]), (uint32_t)((eseq / QN) & 1), abort)) { ok = false; break; }
-        volatile int* rp = reinterpret_cast<volatile int*>(&sh.rec[slot]);
-        const int4 r = make_int4(rp[0], rp[1], rp[2], rp[3]);
-        const uint32_t b = (uint32_t)r.x;
-        if (!mbar_wait(bar(&sh.accf[b]), (accf_par >> b) & 1u, abort)) { ok = false; break; }
-        accf_par ^= 1u << b;
-        tc_fence_after();
-        uint32_t v[32];
-        tmem_ld32(tmem + ((uint32_t)(lq * 32) << 16) + b * BN + ch * 32, v);
-        tmem_wait_ld();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bar(&sh.acce[b]));
-        const int shl = r.y;
-        if (shl < 32) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) zlo[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << shl;
-        } else {
-          const int sh2 = shl - 32;
-#pragma unroll
-          for (int j = 0; j < 32; ++j) zhi[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << sh2;
-        }
-        ++eseq;
-        if (r.z & 1) break;
+      // replay the issuer's schedule: buffers of k-block 0, then mid-tile drains ordered by
+      // (k-block, diagonal), then the final buffers of diagonals 0..S-1
+      const int S = P->s, nkb = P->nkb;
+      const bool stag = stagger_of(nkb);
+      uint32_t bufs[MAX_LEVEL];
+      int nxt[MAX_LEVEL], per[MAX_LEVEL];
+      for (int g = S - 1; g >= 0; --g) bufs[g] = er.next();
+      for (int g = 0; g < S; ++g) drain_plan(g, S, stag, nxt[g], per[g]);
+      while (ok) {
+        int kbmin = nkb, gsel = -1;
+        for (int g = 0; g < S; ++g)
+          if (nxt[g] < kbmin) {
+            kbmin = nxt[g];
+            gsel = g;
+          }
+        if (gsel < 0) break;
+        ok = drain_into(sh, tmem, lq, ch, lane, bufs[gsel], 8 * (S - 1 - gsel), accf_par, abort, zlo, zhi);
+        er.posted(bufs[gsel]);
+        bufs[gsel] = er.next();
+        nxt[gsel] += per[gsel];
+      }
+      for (int g = 0; g < S && ok; ++g) {
+        ok = drain_into(sh, tmem, lq, ch, lane, bufs[g], 8 * (S - 1 - g), accf_par, abort, zlo, zhi);
+        er.posted(bufs[g]);
       }
       if (!ok) break;
-      // ---- one rounding to FP64, scaling, store
+      // ---- one rounding to FP64, scaling; stores staged through shared memory, 8 columns at a time,
+      //      so that one warp store writes 4 rows x 64 contiguous bytes
       const int M = P->M, N = P->N, s = P->s, mode = P->mode;
       const int row = mb * TILE_M + lq * 32 + lane;
-      if (row < M) {
-        const int* __restrict__ eb = P->eb;
-        const int ea = __ldg(P->ea + row) - 8 * s - 6;
-        const int col0 = nb * BN + ch * 32;
-        const int ncol = min(32, N - col0);
-        if (mode == OUT_DENSE) {
-          double* crow = P->C + (long long)row * P->ldc + col0;
-          const double alpha = P->alpha, beta = P->beta;
-          const bool plain = (alpha == 1.0) && (beta == 0.0);
+      const bool rowok = row < M;
+      const int col0 = nb * BN + ch * 32;
+      const int ncol = min(32, N - col0);
+      const int* __restrict__ eb = P->eb;
+      const int ea = rowok ? __ldg(P->ea + row) - 8 * s - 6 : 0;
+      double* crow = nullptr;
+      if (rowok) crow = (mode == OUT_DENSE ? P->C + (long long)row * P->ldc : P->C + __ldg(P->rowdst + row)) + col0;
+      const double alpha = P->alpha, beta = P->beta;
+      const bool plain = (mode != OUT_DENSE) || ((alpha == 1.0) && (beta == 0.0));
+      unsigned long long mx = 0;
+      double* stg = out_stage + (warp - 2) * 32 * OUT_LD;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            if (j < ncol) {
-              const __int128 Z = ((__int128)zhi[j] << 32) + (__int128)zlo[j];
-              double c = int128_to_double(Z, ea + __ldg(eb + col0 + j));
+      for (int c8 = 0; c8 < 4; ++c8) {
+        if (c8 * 8 < ncol) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int jj = c8 * 8 + j;
+            double v = 0.0;
+            if (rowok && jj < ncol) {
+              v = split_to_double(zhi[jj], zlo[jj], ea + __ldg(eb + col0 + jj));
               if (!plain) {
-                c = __dmul_rn(alpha, c);
-                if (beta != 0.0) c = __dadd_rn(c, __dmul_rn(beta, crow[j]));
+                v = __dmul_rn(alpha, v);
+                if (beta != 0.0) v = __dadd_rn(v, __dmul_rn(beta, crow[jj]));
               }
-              crow[j] = c;
-            }
-          }
-        } else {
-          double* crow = P->C + __ldg(P->rowdst + row) + col0;
-          unsigned long long mx = 0;
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            if (j < ncol) {
-              const __int128 Z = ((__int128)zhi[j] << 32) + (__int128)zlo[j];
-              const double c = int128_to_double(Z, ea + __ldg(eb + col0 + j));
-              crow[j] = c;
-              const unsigned long long bb = (unsigned long long)__double_as_longlong(c) & 0x7FFFFFFFFFFFFFFFull;
+              const unsigned long long bb = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
               mx = bb > mx ? bb : mx;
             }
+            stg[lane * OUT_LD + j] = v;
           }
-          unsigned long long* rmax = P->rowmax;
-          if (rmax && mx) atomicMax(rmax + __ldg(P->rowslot + row), mx);
+          __syncwarp();
+#pragma unroll
+          for (int p = 0; p < 8; ++p) {
+            const int r = p * 4 + (lane >> 3), cc = lane & 7;
+            double* base = reinterpret_cast<double*>(
+                __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(crow), r));
+            if (base && c8 * 8 + cc < ncol) base[c8 * 8 + cc] = stg[r * OUT_LD + cc];
+          }
+          __syncwarp();
         }
       }
+      if (mode != OUT_DENSE && rowok && mx && P->rowmax) atomicMax(P->rowmax + __ldg(P->rowslot + row), mx);
     }
   }
 

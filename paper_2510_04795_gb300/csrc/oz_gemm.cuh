@@ -8,7 +8,6 @@ constexpr int BN = 64;              // output tile columns (MMA N)
 constexpr int NBUF = 512 / BN;      // TMEM accumulator buffers of BN columns
 constexpr int NSTAGE = 4;           // shared-memory pipeline stages
 constexpr int MAX_LEVEL = 8;        // slice levels supported by the BN = 64 kernel (one buffer per diagonal)
-constexpr int QN = 16;              // drain-record ring
 
 enum : int { OUT_DENSE = 0, OUT_ROWTABLE = 1 };
 

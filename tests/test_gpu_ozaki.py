@@ -168,3 +168,18 @@ def test_gemm_error_within_bound_and_decreasing(ctx):
         if prev is not None and prev > 1e-300:
             assert mx <= prev
         prev = mx
+
+
+@pytest.mark.parametrize("scale_a,scale_b", [(1e-160, 1e-160), (1e-200, 1e-110), (1e150, 1e155), (2.0 ** -540, 2.0 ** -530)])
+def test_gemm_extreme_exponents(ctx, scale_a, scale_b):
+    """Results in the subnormal range, near overflow, and rounding across the normal/subnormal edge."""
+    import paper_2510_04795_gb300 as oz
+    rng = np.random.default_rng(15)
+    A = rng.normal(size=(70, 40)) * scale_a
+    B = rng.normal(size=(40, 65)) * scale_b
+    A[0] *= 1e-6
+    for S in (3, 7):
+        C = oz.ozaki_gemm(ctx, _dev(A), _dev(B), slices=S).cpu().numpy()
+        ctx.status()
+        ref = ozaki.ozaki_gemm(A, B, S)
+        assert np.array_equal(C.view(np.int64), ref.view(np.int64))
