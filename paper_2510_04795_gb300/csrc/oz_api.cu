@@ -229,7 +229,7 @@ extern "C" int ozaki_gemm(oz_ctx* c, int m, int n, int k, double alpha, const do
   P.M = m; P.N = n; P.nkb = o.nkb; P.SA = S; P.SB = S; P.s = s;
   P.mode = oz::OUT_DENSE; P.C = C; P.ldc = ldc; P.alpha = alpha; P.beta = beta;
   int ntiles = o.nrbA * o.nrbB;
-  OZ_CU(oz::launch_gemm(nullptr, nullptr, ntiles, c->nsm, &P, c->d_flags + 1, st));
+  OZ_CU(oz::launch_gemm(nullptr, nullptr, ntiles, c->nsm, &P, 0, c->d_flags + 1, st));
   return OZ_OK;
 }
 
@@ -274,7 +274,7 @@ extern "C" int ozaki_slice_products(oz_ctx* c, int m, int n, int k, const double
       P.ea = sevens; P.eb = sevens;
       P.M = m; P.N = n; P.nkb = o.nkb; P.SA = S; P.SB = S; P.s = 1;
       P.mode = oz::OUT_DENSE; P.C = Pout + (size_t)(t * S + u) * m * n; P.ldc = n; P.alpha = 1.0; P.beta = 0.0;
-      OZ_CU(oz::launch_gemm(nullptr, nullptr, o.nrbA * o.nrbB, c->nsm, &P, c->d_flags + 1, st));
+      OZ_CU(oz::launch_gemm(nullptr, nullptr, o.nrbA * o.nrbB, c->nsm, &P, 0, c->d_flags + 1, st));
     }
   return OZ_OK;
 }
@@ -360,12 +360,12 @@ int oz_heff_s::enqueue(cudaStream_t st, bool capturing) {
     OZ_CU(oz::launch_rowmax(dSegPsi, nullptr, nsegPsi, uPsiM, ctx->d_flags, st));
     OZ_CU(oz::launch_digits(dSegPsi, nullptr, nsegPsi, uPsiD, S, st));
     OZ_CU(cudaEventRecordWithFlags(ev[1], st, evf));
-    OZ_CU(oz::launch_gemm(dP1, dT1, nt1, ctx->nsm, nullptr, ctx->d_flags + 1, st));
+    OZ_CU(oz::launch_gemm(dP1, dT1, nt1, ctx->nsm, nullptr, s, ctx->d_flags + 1, st));
     OZ_CU(cudaEventRecordWithFlags(ev[2], st, evf));
     OZ_CU(oz::launch_digits(dSegA2, nullptr, nsegA2, uA2D, S, st));
     if (zero_y) OZ_CU(cudaMemsetAsync(dY, 0, (size_t)dim * 8, st));
     OZ_CU(cudaEventRecordWithFlags(ev[3], st, evf));
-    OZ_CU(oz::launch_gemm(dP2, dT2, nt2, ctx->nsm, nullptr, ctx->d_flags + 1, st));
+    OZ_CU(oz::launch_gemm(dP2, dT2, nt2, ctx->nsm, nullptr, s, ctx->d_flags + 1, st));
     OZ_CU(cudaEventRecordWithFlags(ev[4], st, evf));
     return OZ_OK;
   }

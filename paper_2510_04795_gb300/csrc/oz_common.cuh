@@ -265,4 +265,51 @@ OZ_DEVICE_INLINE double split_to_double(long long zhi, long long zlo, int E) {
   return __longlong_as_double((long long)(sign | ((unsigned long long)(e2 + 1023) << 52) | (m & ((1ull << 52) - 1))));
 }
 
+// Same rounding as split_to_double with 32-bit word arithmetic only: Z = zhi * 2^32 + zlo is
+// formed as a 96-bit two's-complement number w2:w1:w0 (|zhi|, |zlo| < 2^62 so |Z| < 2^95),
+// normalised by whole words and one funnel shift, rounded to 53 bits (ties to even) with a sticky
+// bit, and assembled directly; results outside the normal range take the general path.
+OZ_DEVICE_INLINE double z96_to_double(long long zhi, long long zlo, int E) {
+  const uint32_t l0 = (uint32_t)zlo, l1 = (uint32_t)((unsigned long long)zlo >> 32);
+  const uint32_t h0 = (uint32_t)zhi, h1 = (uint32_t)((unsigned long long)zhi >> 32);
+  const uint32_t sx = (uint32_t)((int32_t)l1 >> 31);
+  uint32_t w0 = l0, w1, w2;
+  asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, %5;" : "=r"(w1), "=r"(w2) : "r"(l1), "r"(h0), "r"(h1), "r"(sx));
+  const uint32_t sign = w2 & 0x80000000u;
+  if (sign) asm("sub.cc.u32 %0, 0, %0;\n\tsubc.cc.u32 %1, 0, %1;\n\tsubc.u32 %2, 0, %2;" : "+r"(w0), "+r"(w1), "+r"(w2));
+  if ((w0 | w1 | w2) == 0u) return 0.0;
+  int lz = 0;
+  if (w2 == 0u) {
+    w2 = w1;
+    w1 = w0;
+    w0 = 0u;
+    lz = 32;
+    if (w2 == 0u) {
+      w2 = w1;
+      w1 = 0u;
+      lz = 64;
+    }
+  }
+  const int sft = __clz((int)w2);
+  if (sft) {
+    w2 = __funnelshift_l(w1, w2, sft);
+    w1 = __funnelshift_l(w0, w1, sft);
+    w0 <<= sft;
+  }
+  lz += sft;
+  int e2 = 95 - lz + E;
+  uint32_t mh = w2 >> 11, ml = (w2 << 21) | (w1 >> 11);
+  const uint32_t g = w1 & 0x7FFu;
+  if (g > 0x400u || (g == 0x400u && (w0 != 0u || (ml & 1u)))) {
+    asm("add.cc.u32 %0, %0, 1;\n\taddc.u32 %1, %1, 0;" : "+r"(ml), "+r"(mh));
+    if (mh >> 21) {
+      mh = 1u << 20;
+      ml = 0u;
+      e2 += 1;
+    }
+  }
+  if (e2 < -1022 || e2 > 1023) return int128_to_double(((__int128)zhi << 32) + (__int128)zlo, E);
+  return __hiloint2double((int)(sign | ((uint32_t)(e2 + 1023) << 20) | (mh & 0xFFFFFu)), (int)ml);
+}
+
 }  // namespace oz

@@ -8,16 +8,17 @@
 // accumulator group holds at most GROUP_TERMS = 1008 products, so each FP32 partial sum is an
 // integer below 2^24 and the accumulation is exact (checked on the device against int64).
 //
-// One CTA per SM, persistent over a tile list; 10 warps:
-//   warp 0       producer: cp.async.bulk of pre-tiled digit planes into an NSTAGE ring
+// One CTA per SM, persistent over a tile list; 18 warps:
+//   warp 0       producer: cp.async.bulk of pre-tiled digit planes into a ring of shared-memory stages
 //   warp 1       TMEM owner and single-thread MMA issuer; diagonal g = t+u (0-based) of the slice
 //                grid accumulates into its own TMEM buffer (BN columns), A reused through the
 //                collector across the u loop; a buffer whose group is full is handed to the
 //                epilogue ("drain": one tcgen05.commit) and replaced by a free one
-//   warps 2..9   epilogue: replays the same deterministic drain/buffer schedule, reads each
-//                drained buffer, adds q * 256^(s-1-g) into exact running sums per output element,
-//                then rounds once to FP64 scaled by 2^(ea+eb-8s-6), applies alpha/beta, stores
-//                (and for the row-table mode records a per-row |max| for the next slicing).
+//   warps 2..17  epilogue, 4 warps per TMEM lane quarter, 16 columns each: replays the same
+//                deterministic drain/buffer schedule, reads each drained buffer, adds
+//                q * 256^(s-1-g) into exact running sums per output element, then rounds once to
+//                FP64 scaled by 2^(ea+eb-8s-6), applies alpha/beta, stores (and for the row-table
+//                mode records a per-row |max| for the next slicing).
 // The drain schedule: diagonal g takes p = 16(g+1) products per k-block; its groups hold
 // floor(GROUP_TERMS/p) k-blocks (the first group of long tiles is shortened per diagonal so that the
 // drains of different diagonals do not coincide).  The first k-block of a tile is issued diagonal by
@@ -27,22 +28,48 @@
 
 namespace oz {
 
-constexpr int A_TILE_BYTES = TILE_M * KB * 2;   // 8 KB per plane
-constexpr int B_TILE_BYTES = BN * KB * 2;       // 4 KB per plane
-constexpr int STAGE_BYTES = MAX_LEVEL * (A_TILE_BYTES + B_TILE_BYTES);
-constexpr int NTHREADS = 320;
-constexpr int OUT_LD = 9;                             // staging row stride (doubles), breaks bank conflicts
-constexpr int OUT_STAGE_BYTES = 8 * 32 * OUT_LD * 8;  // 8 epilogue warps x 32 rows x 8 columns
+constexpr int A_TILE_BYTES = TILE_M * KB * 2;             // 4 KB per plane
+constexpr int B_TILE_BYTES = BN * KB * 2;                 // 2 KB per plane
+constexpr int PLANE_BYTES = A_TILE_BYTES + B_TILE_BYTES;  // one slice plane of A and of B^T per k-block
+constexpr int EPI_WARPS = 16;
+constexpr int CW = BN / (EPI_WARPS / 4);                  // columns per epilogue warp (16)
+constexpr int NTHREADS = 32 * (2 + EPI_WARPS);
+constexpr int MAX_STAGES = 4;
+// Final-stage staging: per epilogue warp, 32 rows x ZC columns of 16-byte exact sums (converted in
+// place to doubles); row stride (ZC + 1) x 16 bytes against bank conflicts.
+constexpr int ZC = 4;
+constexpr int ZS_LD = ZC + 1;
+constexpr int ZS_BYTES = EPI_WARPS * 32 * ZS_LD * 16;
+constexpr int SMEM_LIMIT = 232448;                        // opt-in shared memory per block
 
 struct Shared {
-  unsigned long long full[NSTAGE], empty[NSTAGE], accf[NBUF], acce[NBUF], fin;
+  unsigned long long full[MAX_STAGES], empty[MAX_STAGES], accf[NBUF], acce[NBUF], fin;
   uint32_t tmem;
   int abort;
 };
 
-size_t gemm_smem_bytes() { return (size_t)NSTAGE * STAGE_BYTES + OUT_STAGE_BYTES + sizeof(Shared) + 1024; }
+// pipeline stages that fit next to the staging area for slice level smax
+int gemm_stages(int smax) {
+  const int avail = SMEM_LIMIT - ZS_BYTES - (int)sizeof(Shared) - 1024;
+  const int n = avail / (smax * PLANE_BYTES);
+  return n < MAX_STAGES ? n : MAX_STAGES;
+}
+size_t gemm_smem_bytes(int smax) {
+  return (size_t)gemm_stages(smax) * smax * PLANE_BYTES + ZS_BYTES + sizeof(Shared) + 1024;
+}
 
 __device__ __forceinline__ uint32_t bar(const unsigned long long* p) { return smem_u32(p); }
+
+// position in the stage ring: stage index and the parity of its current fill
+struct Ring {
+  int stg, ph, n;
+  __device__ __forceinline__ void advance() {
+    if (++stg == n) {
+      stg = 0;
+      ph ^= 1;
+    }
+  }
+};
 
 // Deterministic TMEM buffer assignment, replayed identically by the MMA issuer and the epilogue:
 // the n-th acquisition returns buffer n while n < NBUF, afterwards the buffer of post n - NBUF.
@@ -71,7 +98,7 @@ __device__ __forceinline__ void drain_plan(int g, int S, bool stagger, int& firs
 __device__ __forceinline__ bool stagger_of(int nkb) { return nkb >= 64; }
 
 struct MmaCtl {
-  long long it;       // k-block iterations issued (ring position)
+  Ring rg;
   BufRing r;
   uint32_t acce_par;  // per buffer parity of the next "drained" wait
 };
@@ -92,7 +119,8 @@ __device__ __forceinline__ void post(Shared& sh, MmaCtl& c, uint32_t b) {
 }
 
 template <int S>
-__device__ void mma_tile(Shared& sh, MmaCtl& c, uint32_t tmem, uint32_t stage0, int nkb, volatile int* abort) {
+__device__ void mma_tile(Shared& sh, MmaCtl& c, uint32_t tmem, uint32_t stage0, uint32_t stage_bytes, uint32_t boff,
+                         int nkb, volatile int* abort) {
   constexpr uint32_t IDESC = idesc_f16(TILE_M, BN);
   uint32_t buf[S];
   int nxt[S], per[S];
@@ -105,11 +133,10 @@ __device__ void mma_tile(Shared& sh, MmaCtl& c, uint32_t tmem, uint32_t stage0, 
   }
   // ---- k-block 0: diagonal by diagonal (heaviest first), each as soon as its buffer is free
   {
-    const int stg = (int)(c.it % NSTAGE);
-    if (!mbar_wait(bar(&sh.full[stg]), (uint32_t)((c.it / NSTAGE) & 1), abort)) return;
-    const uint32_t aaddr = stage0 + stg * STAGE_BYTES;
+    if (!mbar_wait(bar(&sh.full[c.rg.stg]), (uint32_t)c.rg.ph, abort)) return;
+    const uint32_t aaddr = stage0 + c.rg.stg * stage_bytes;
     const uint64_t ad0 = smem_desc(aaddr, 128, 128 * KB_CM);
-    const uint64_t bd0 = smem_desc(aaddr + MAX_LEVEL * A_TILE_BYTES, 128, 128 * KB_CM);
+    const uint64_t bd0 = smem_desc(aaddr + boff, 128, 128 * KB_CM);
 #pragma unroll
     for (int g = S - 1; g >= 0; --g) {
       buf[g] = acquire(sh, c, abort);
@@ -119,8 +146,8 @@ __device__ void mma_tile(Shared& sh, MmaCtl& c, uint32_t tmem, uint32_t stage0, 
         mma_f16<0>(d, ad0 + (uint64_t)((t * A_TILE_BYTES) >> 4), bd0 + (uint64_t)(((g - t) * B_TILE_BYTES) >> 4), IDESC,
                    t > 0 ? 1u : 0u);
     }
-    tc_commit(bar(&sh.empty[stg]));
-    c.it++;
+    tc_commit(bar(&sh.empty[c.rg.stg]));
+    c.rg.advance();
   }
   uint32_t fresh = 0u;  // diagonals whose current buffer has not been written yet
   for (int kb = 1; kb < nkb; ++kb) {
@@ -137,11 +164,10 @@ __device__ void mma_tile(Shared& sh, MmaCtl& c, uint32_t tmem, uint32_t stage0, 
         nmin = min(nmin, nxt[g]);
       }
     }
-    const int stg = (int)(c.it % NSTAGE);
-    if (!mbar_wait(bar(&sh.full[stg]), (uint32_t)((c.it / NSTAGE) & 1), abort)) return;
-    const uint32_t aaddr = stage0 + stg * STAGE_BYTES;
+    if (!mbar_wait(bar(&sh.full[c.rg.stg]), (uint32_t)c.rg.ph, abort)) return;
+    const uint32_t aaddr = stage0 + c.rg.stg * stage_bytes;
     const uint64_t ad0 = smem_desc(aaddr, 128, 128 * KB_CM);
-    const uint64_t bd0 = smem_desc(aaddr + MAX_LEVEL * A_TILE_BYTES, 128, 128 * KB_CM);
+    const uint64_t bd0 = smem_desc(aaddr + boff, 128, 128 * KB_CM);
 #pragma unroll
     for (int t = 0; t < S; ++t) {
       const uint64_t ad = ad0 + (uint64_t)((t * A_TILE_BYTES) >> 4);
@@ -160,34 +186,34 @@ __device__ void mma_tile(Shared& sh, MmaCtl& c, uint32_t tmem, uint32_t stage0, 
       }
     }
     fresh = 0u;
-    tc_commit(bar(&sh.empty[stg]));
-    c.it++;
+    tc_commit(bar(&sh.empty[c.rg.stg]));
+    c.rg.advance();
   }
 #pragma unroll
   for (int g = 0; g < S; ++g) post(sh, c, buf[g]);
 }
 
 // Epilogue side of one drain: wait until the MMAs into buffer b are complete, read this warp's
-// 32 x 32 slice, release the buffer, add q * 2^shl into the exact running sums.
-__device__ __forceinline__ bool drain_into(Shared& sh, uint32_t tmem, int lq, int ch, int lane, uint32_t b, int shl,
-                                           uint32_t& accf_par, volatile int* abort, long long (&zlo)[32],
-                                           long long (&zhi)[32]) {
+// 32 x CW slice, release the buffer, add q * 2^shl into the exact running sums.
+__device__ __forceinline__ bool drain_into(Shared& sh, uint32_t tmem, int lq, int cg, int lane, uint32_t b, int shl,
+                                           uint32_t& accf_par, volatile int* abort, long long (&zlo)[CW],
+                                           long long (&zhi)[CW]) {
   if (!mbar_wait(bar(&sh.accf[b]), (accf_par >> b) & 1u, abort)) return false;
   accf_par ^= 1u << b;
   tc_fence_after();
-  uint32_t v[32];
-  tmem_ld32(tmem + ((uint32_t)(lq * 32) << 16) + b * BN + ch * 32, v);
+  uint32_t v[CW];
+  tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + b * BN + cg * CW, v);
   tmem_wait_ld();
   tc_fence_before();
   __syncwarp();
   if (lane == 0) mbar_arrive(bar(&sh.acce[b]));
   if (shl < 32) {
 #pragma unroll
-    for (int j = 0; j < 32; ++j) zlo[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << shl;
+    for (int j = 0; j < CW; ++j) zlo[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << shl;
   } else {
     const int sh2 = shl - 32;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) zhi[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << sh2;
+    for (int j = 0; j < CW; ++j) zhi[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << sh2;
   }
   return true;
 }
@@ -209,23 +235,24 @@ __device__ __forceinline__ void tile_of(const GemmTile* tiles, const GemmProblem
 
 __global__ void __launch_bounds__(NTHREADS, 1)
     gemm_kernel(const GemmProblem* __restrict__ probs, const GemmTile* __restrict__ tiles, int ntiles,
-                const __grid_constant__ GemmProblem single, int* __restrict__ err) {
+                const __grid_constant__ GemmProblem single, int smax, int nstage, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  double* out_stage = reinterpret_cast<double*>(smem + NSTAGE * STAGE_BYTES);
-  Shared& sh = *reinterpret_cast<Shared*>(smem + NSTAGE * STAGE_BYTES + OUT_STAGE_BYTES);
+  const uint32_t stage_bytes = (uint32_t)(smax * PLANE_BYTES), boff = (uint32_t)(smax * A_TILE_BYTES);
+  longlong2* zstage = reinterpret_cast<longlong2*>(smem + nstage * stage_bytes);
+  Shared& sh = *reinterpret_cast<Shared*>(smem + nstage * stage_bytes + ZS_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* abort = &sh.abort;
   const uint32_t stage0 = smem_u32(smem);
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < NSTAGE; ++i) {
+    for (int i = 0; i < nstage; ++i) {
       mbar_init(bar(&sh.full[i]), 1);
       mbar_init(bar(&sh.empty[i]), 1);
     }
     for (int i = 0; i < NBUF; ++i) {
       mbar_init(bar(&sh.accf[i]), 1);
-      mbar_init(bar(&sh.acce[i]), 8);
+      mbar_init(bar(&sh.acce[i]), EPI_WARPS);
     }
     mbar_init(bar(&sh.fin), 1);
     sh.abort = 0;
@@ -240,7 +267,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 0) {
     // ------------------------------------------------------------------ producer
     if (lane == 0) {
-      long long it = 0;
+      Ring rg{0, 0, nstage};
+      long long fills = 0;
       for (int idx = blockIdx.x; idx < ntiles && !*abort; idx += gridDim.x) {
         const GemmProblem* P;
         int mb, nb;
@@ -248,41 +276,50 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int nkb = P->nkb, s = P->s, SA = P->SA, SB = P->SB;
         const char* Ab = reinterpret_cast<const char*>(P->A) + (long long)mb * nkb * SA * A_TILE_BYTES;
         const char* Bb = reinterpret_cast<const char*>(P->B) + (long long)nb * nkb * SB * B_TILE_BYTES;
-        for (int kb = 0; kb < nkb; ++kb, ++it) {
-          const int stg = (int)(it % NSTAGE);
-          if (it >= NSTAGE && !mbar_wait(bar(&sh.empty[stg]), (uint32_t)(((it / NSTAGE) - 1) & 1), abort)) break;
-          mbar_expect_tx(bar(&sh.full[stg]), (uint32_t)(s * (A_TILE_BYTES + B_TILE_BYTES)));
-          const uint32_t dA = stage0 + stg * STAGE_BYTES;
-          bulk_g2s(dA, Ab + (long long)kb * SA * A_TILE_BYTES, (uint32_t)(s * A_TILE_BYTES), bar(&sh.full[stg]));
-          bulk_g2s(dA + MAX_LEVEL * A_TILE_BYTES, Bb + (long long)kb * SB * B_TILE_BYTES,
-                   (uint32_t)(s * B_TILE_BYTES), bar(&sh.full[stg]));
+        bool stop = false;
+        for (int kb = 0; kb < nkb; ++kb) {
+          // a stage is refilled once the MMAs of its previous fill have completed
+          if (fills >= nstage && !mbar_wait(bar(&sh.empty[rg.stg]), (uint32_t)(rg.ph ^ 1), abort)) {
+            stop = true;
+            break;
+          }
+          mbar_expect_tx(bar(&sh.full[rg.stg]), (uint32_t)(s * PLANE_BYTES));
+          const uint32_t dA = stage0 + rg.stg * stage_bytes;
+          bulk_g2s(dA, Ab + (long long)kb * SA * A_TILE_BYTES, (uint32_t)(s * A_TILE_BYTES), bar(&sh.full[rg.stg]));
+          bulk_g2s(dA + boff, Bb + (long long)kb * SB * B_TILE_BYTES, (uint32_t)(s * B_TILE_BYTES),
+                   bar(&sh.full[rg.stg]));
+          ++fills;
+          rg.advance();
         }
+        if (stop) break;
       }
-      // let the copies still in flight land before the CTA can exit
-      for (long long j = it - NSTAGE; j < it; ++j) {
-        if (j < 0) continue;
-        volatile int never = 0;
-        mbar_wait(bar(&sh.full[j % NSTAGE]), (uint32_t)((j / NSTAGE) & 1), &never);
+      // let the copies still in flight land before the CTA can exit: wait for the last fill of
+      // every stage that was filled
+      volatile int never = 0;
+      for (int i = 0; i < nstage && i < fills; ++i) {
+        rg.stg = rg.stg == 0 ? nstage - 1 : rg.stg - 1;
+        if (rg.stg == nstage - 1) rg.ph ^= 1;
+        mbar_wait(bar(&sh.full[rg.stg]), (uint32_t)rg.ph, &never);
       }
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      MmaCtl c{0, BufRing{0u, 0, 0}, 0u};
+      MmaCtl c{Ring{0, 0, nstage}, BufRing{0u, 0, 0}, 0u};
       for (int idx = blockIdx.x; idx < ntiles && !*abort; idx += gridDim.x) {
         const GemmProblem* P;
         int mb, nb;
         tile_of(tiles, probs, single, idx, P, mb, nb);
         const int nkb = P->nkb;
         switch (P->s) {
-          case 1: mma_tile<1>(sh, c, tmem, stage0, nkb, abort); break;
-          case 2: mma_tile<2>(sh, c, tmem, stage0, nkb, abort); break;
-          case 3: mma_tile<3>(sh, c, tmem, stage0, nkb, abort); break;
-          case 4: mma_tile<4>(sh, c, tmem, stage0, nkb, abort); break;
-          case 5: mma_tile<5>(sh, c, tmem, stage0, nkb, abort); break;
-          case 6: mma_tile<6>(sh, c, tmem, stage0, nkb, abort); break;
-          case 7: mma_tile<7>(sh, c, tmem, stage0, nkb, abort); break;
-          case 8: mma_tile<8>(sh, c, tmem, stage0, nkb, abort); break;
+          case 1: mma_tile<1>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
+          case 2: mma_tile<2>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
+          case 3: mma_tile<3>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
+          case 4: mma_tile<4>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
+          case 5: mma_tile<5>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
+          case 6: mma_tile<6>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
+          case 7: mma_tile<7>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
+          case 8: mma_tile<8>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
           default: *abort = 1; break;
         }
       }
@@ -293,19 +330,29 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else {
     // ------------------------------------------------------------------ epilogue
-    const int lq = warp & 3;            // TMEM lane quarter this warp may access
-    const int ch = (warp - 2) >> 2;     // column half of the BN-wide tile
+    const int lq = warp & 3;              // TMEM lane quarter this warp may access
+    const int cg = (warp - 2) >> 2;       // column group of the BN-wide tile
     uint32_t accf_par = 0;
     BufRing er{0u, 0, 0};
+    longlong2* zs = zstage + (warp - 2) * 32 * ZS_LD;
     for (int idx = blockIdx.x; idx < ntiles && !*abort; idx += gridDim.x) {
       const GemmProblem* P;
       int mb, nb;
       tile_of(tiles, probs, single, idx, P, mb, nb);
+      // per-tile operands of the final stage, loaded now so that their latency hides behind the drains
+      const int M = P->M, N = P->N, mode = P->mode;
+      const int row = mb * TILE_M + lq * 32 + lane;
+      const bool rowok = row < M;
+      const int col0 = nb * BN + cg * CW;
+      const int ebl = (lane < CW && col0 + lane < N) ? __ldg(P->eb + col0 + lane) : 0;
+      const int ea_raw = rowok ? __ldg(P->ea + row) : 0;
+      double* crow = nullptr;
+      if (rowok) crow = (mode == OUT_DENSE ? P->C + (long long)row * P->ldc : P->C + __ldg(P->rowdst + row)) + col0;
       // exact running sum Z = zhi * 2^32 + zlo; drains with shift < 32 go to zlo, the others to zhi
       // (each part stays below 2^62 in magnitude for levels <= 8 and fewer than 2^13 groups per diagonal)
-      long long zlo[32], zhi[32];
+      long long zlo[CW], zhi[CW];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
+      for (int j = 0; j < CW; ++j) {
         zlo[j] = 0ll;
         zhi[j] = 0ll;
       }
@@ -326,40 +373,37 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             gsel = g;
           }
         if (gsel < 0) break;
-        ok = drain_into(sh, tmem, lq, ch, lane, bufs[gsel], 8 * (S - 1 - gsel), accf_par, abort, zlo, zhi);
+        ok = drain_into(sh, tmem, lq, cg, lane, bufs[gsel], 8 * (S - 1 - gsel), accf_par, abort, zlo, zhi);
         er.posted(bufs[gsel]);
         bufs[gsel] = er.next();
         nxt[gsel] += per[gsel];
       }
       for (int g = 0; g < S && ok; ++g) {
-        ok = drain_into(sh, tmem, lq, ch, lane, bufs[g], 8 * (S - 1 - g), accf_par, abort, zlo, zhi);
+        ok = drain_into(sh, tmem, lq, cg, lane, bufs[g], 8 * (S - 1 - g), accf_par, abort, zlo, zhi);
         er.posted(bufs[g]);
       }
       if (!ok) break;
-      // ---- one rounding to FP64, scaling; stores staged through shared memory, 8 columns at a time,
-      //      so that one warp store writes 4 rows x 64 contiguous bytes
-      const int M = P->M, N = P->N, s = P->s, mode = P->mode;
-      const int row = mb * TILE_M + lq * 32 + lane;
-      const bool rowok = row < M;
-      const int col0 = nb * BN + ch * 32;
-      const int ncol = min(32, N - col0);
-      const int* __restrict__ eb = P->eb;
-      const int ea = rowok ? __ldg(P->ea + row) - 8 * s - 6 : 0;
-      double* crow = nullptr;
-      if (rowok) crow = (mode == OUT_DENSE ? P->C + (long long)row * P->ldc : P->C + __ldg(P->rowdst + row)) + col0;
+      // ---- one rounding to FP64, scaling; the exact sums pass through shared memory ZC columns at a
+      //      time so that the conversion code exists once (compact loop), and the stores are coalesced
+      const int ncol = min(CW, N - col0);
+      const int ea = ea_raw - 8 * S - 6;
       const double alpha = P->alpha, beta = P->beta;
       const bool plain = (mode != OUT_DENSE) || ((alpha == 1.0) && (beta == 0.0));
       unsigned long long mx = 0;
-      double* stg = out_stage + (warp - 2) * 32 * OUT_LD;
 #pragma unroll
-      for (int c8 = 0; c8 < 4; ++c8) {
-        if (c8 * 8 < ncol) {
+      for (int c4 = 0; c4 < CW / ZC; ++c4) {
+        if (c4 * ZC < ncol) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int jj = c8 * 8 + j;
+          for (int j = 0; j < ZC; ++j) zs[lane * ZS_LD + j] = make_longlong2(zhi[c4 * ZC + j], zlo[c4 * ZC + j]);
+          __syncwarp();
+#pragma unroll 1
+          for (int j = 0; j < ZC; ++j) {
+            const int jj = c4 * ZC + j;
+            const int ebj = __shfl_sync(0xffffffffu, ebl, jj);
             double v = 0.0;
             if (rowok && jj < ncol) {
-              v = split_to_double(zhi[jj], zlo[jj], ea + __ldg(eb + col0 + jj));
+              const longlong2 z = zs[lane * ZS_LD + j];
+              v = z96_to_double(z.x, z.y, ea + ebj);
               if (!plain) {
                 v = __dmul_rn(alpha, v);
                 if (beta != 0.0) v = __dadd_rn(v, __dmul_rn(beta, crow[jj]));
@@ -367,15 +411,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               const unsigned long long bb = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
               mx = bb > mx ? bb : mx;
             }
-            stg[lane * OUT_LD + j] = v;
+            reinterpret_cast<double*>(zs + lane * ZS_LD + j)[0] = v;
           }
           __syncwarp();
-#pragma unroll
-          for (int p = 0; p < 8; ++p) {
-            const int r = p * 4 + (lane >> 3), cc = lane & 7;
-            double* base = reinterpret_cast<double*>(
-                __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(crow), r));
-            if (base && c8 * 8 + cc < ncol) base[c8 * 8 + cc] = stg[r * OUT_LD + cc];
+          // coalesced stores: each pass writes (32 / ZC) rows x ZC consecutive doubles
+#pragma unroll 1
+          for (int p = 0; p < ZC; ++p) {
+            const int r = p * (32 / ZC) + lane / ZC, cc = lane % ZC;
+            double* base =
+                reinterpret_cast<double*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(crow), r));
+            if (base && c4 * ZC + cc < ncol) base[c4 * ZC + cc] = reinterpret_cast<const double*>(zs + r * ZS_LD + cc)[0];
           }
           __syncwarp();
         }
@@ -394,18 +439,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 cudaError_t launch_gemm(const GemmProblem* d_probs, const GemmTile* d_tiles, int ntiles, int grid,
-                        const GemmProblem* single, int* d_err, cudaStream_t st) {
+                        const GemmProblem* single, int smax, int* d_err, cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
   static bool attr = false;
-  const size_t smem = gemm_smem_bytes();
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   GemmProblem one{};
-  if (single) one = *single;
-  gemm_kernel<<<grid < ntiles ? grid : ntiles, NTHREADS, smem, st>>>(d_probs, d_tiles, ntiles, one, d_err);
+  if (single) {
+    one = *single;
+    smax = one.s;
+  }
+  if (smax < 1 || smax > MAX_LEVEL) return cudaErrorInvalidValue;
+  const int nstage = gemm_stages(smax);
+  gemm_kernel<<<grid < ntiles ? grid : ntiles, NTHREADS, gemm_smem_bytes(smax), st>>>(d_probs, d_tiles, ntiles, one,
+                                                                                      smax, nstage, d_err);
   return cudaGetLastError();
 }
 

@@ -6,7 +6,7 @@ namespace oz {
 
 constexpr int BN = 64;              // output tile columns (MMA N)
 constexpr int NBUF = 512 / BN;      // TMEM accumulator buffers of BN columns
-constexpr int NSTAGE = 4;           // shared-memory pipeline stages
+
 constexpr int MAX_LEVEL = 8;        // slice levels supported by the BN = 64 kernel (one buffer per diagonal)
 
 enum : int { OUT_DENSE = 0, OUT_ROWTABLE = 1 };
@@ -34,9 +34,10 @@ struct GemmTile {
   int prob, mb, nb, pad;
 };
 
-size_t gemm_smem_bytes();
-// tiles == nullptr: a single problem (probs[0]) with implicit tiles i -> (i / nnb, i % nnb)
+size_t gemm_smem_bytes(int smax);
+// tiles == nullptr: a single problem (*single) with implicit tiles i -> (i / nnb, i % nnb);
+// otherwise smax is the largest slice level among the launch's problems (sizes the pipeline stages)
 cudaError_t launch_gemm(const GemmProblem* d_probs, const GemmTile* d_tiles, int ntiles, int grid,
-                        const GemmProblem* single, int* d_err, cudaStream_t st);
+                        const GemmProblem* single, int smax, int* d_err, cudaStream_t st);
 
 }  // namespace oz
