@@ -90,6 +90,30 @@ int ozaki_gemm(oz_ctx* ctx, int m, int n, int k, double alpha, const double* d_A
                int ldb, double beta, double* d_C, int ldc, const oz_prec* prec, oz_stream_t stream);
 
 /* ------------------------------------------------------------------------------------------
+ * ozaki_gemm_noalloc: the same emulated product as ozaki_gemm (bit-identical results) for callers
+ * that cannot allocate device memory: code running under a host framework that owns the device's
+ * memory pool, callers inside a region that must not synchronise the device (cudaMalloc and
+ * cudaFree do), or deployments that fix their memory footprint in advance.  The paper has no
+ * counterpart; it is an interface of this library.
+ *   - No context is needed and nothing is allocated: the scratch (digit planes, exponents, row
+ *     maxima, status words) is one statically sized device array of 64 MiB (plus 256 bytes) that
+ *     every GPU loading this library holds until the process exits.
+ *   - A product is rejected with OZ_EINVAL when its scratch would exceed 64 MiB (about
+ *     S * 2 * (m_pad k_pad + n_pad k_pad) bytes, m padded to 128, n to 64, k to 16), when
+ *     k > 1048576, or for the argument errors of ozaki_gemm.  Errors are reported by the return
+ *     code only (oz_last_error is not updated) and device-side conditions (NaN/Inf inputs) are
+ *     not latched: outputs are then unspecified.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) and
+ *     caches it; make that first call before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents; the parts that must start
+ *     at zero are cleared on the stream by each call.  Calls whose execution overlaps on the GPU
+ *     (different streams, or concurrent host threads) race on the array: serialise them.
+ * Arguments as ozaki_gemm; slices S in 1..9, level in 1..min(S,8) (0 = S).
+ * ------------------------------------------------------------------------------------------ */
+int ozaki_gemm_noalloc(int m, int n, int k, double alpha, const double* d_A, int lda, const double* d_B, int ldb,
+                       double beta, double* d_C, int ldc, int slices, int level, oz_stream_t stream);
+
+/* ------------------------------------------------------------------------------------------
  * Verification entry points for the slicing and the slice products (same kernels as ozaki_gemm).
  * ozaki_slice: shared exponents (d_exps[rows]) and digits (d_digits[t][i][j], S x rows x cols,
  *   int8, t = 0 is the most significant) of the rows of A (rows x cols, lda).

@@ -67,6 +67,7 @@ def load():
         "oz_status": (i, [vp, vp]),
         "ozaki_gemm": (i, [vp, i, i, i, d, vp, i, vp, i, d, vp, i, C.POINTER(oz_prec), vp]),
         "ozaki_slice": (i, [vp, i, i, vp, i, i, vp, vp, vp]),
+        "ozaki_gemm_noalloc": (i, [i, i, i, d, vp, i, vp, i, d, vp, i, i, i, vp]),
         "ozaki_slice_products": (i, [vp, i, i, i, vp, i, vp, i, i, vp, vp]),
         "oz_heff_create": (i, [vp, i, C.POINTER(i), C.POINTER(i), i, C.POINTER(oz_task), C.POINTER(oz_prec),
                                C.POINTER(vp)]),
