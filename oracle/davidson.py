@@ -13,7 +13,7 @@ statement of Davidson's method:
            when V reaches max_sub vectors, restart from the Ritz vectors of the 2 lowest
            eigenvalues of G.
 
-Parity: pinned (tests/test_oracle_davidson.py) against numpy.linalg.eigh on
+Parity: pinned (tests/test_oracle_fci_davidson_heff.py) against numpy.linalg.eigh on
 random symmetric matrices and on dense H_eff.
 """
 from __future__ import annotations
@@ -21,8 +21,9 @@ from __future__ import annotations
 import numpy as np
 
 
-def davidson(matvec, diag, x0, tol=1e-10, max_iter=200, max_sub=24):
-    """Returns (theta, x, iterations, converged)."""
+def davidson(matvec, diag, x0, tol=1e-10, max_iter=200, max_sub=24, history=None):
+    """Returns (theta, x, iterations, converged).  If ``history`` is a list, (theta, |r|) of every
+    iteration is appended to it."""
     diag = np.asarray(diag, dtype=np.float64)
     x = np.asarray(x0, dtype=np.float64).copy()
     x /= np.linalg.norm(x)
@@ -38,6 +39,8 @@ def davidson(matvec, diag, x0, tol=1e-10, max_iter=200, max_sub=24):
         x = Vm @ y
         r = Wm @ y - theta * x
         rn = float(np.linalg.norm(r))
+        if history is not None:
+            history.append((theta, rn))
         if rn <= tol:
             return theta, x / np.linalg.norm(x), it, True
         den = theta - diag

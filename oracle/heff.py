@@ -14,6 +14,7 @@ Functions:
  * heff_apply_fp64     plain FP64, one numpy product per block (the error reference).
  * heff_dense          the dense matrix sum_k c_k L_k (x) R_k on vec(psi), brute force
                        (pins heff_apply_fp64 on tiny layouts).
+ * heff_diag           its diagonal (the Davidson preconditioner), pinned by heff_dense.
  * heff_apply_emulated the two-stage emulated definition: for every source sector
                        one Ozaki product of the stacked L blocks with psi[src]; for
                        every target sector one Ozaki product of the concatenated
@@ -59,6 +60,20 @@ def heff_dense(st, Lb: list, Rb: list) -> np.ndarray:
         blk = st.term_coef[k] * np.kron(Lb[t], Rb[t])    # rows (i,j), cols (a,b), row-major pairs
         H[off[d]:off[d + 1], off[s]:off[s + 1]] += blk
     return H
+
+
+def heff_diag(st, Lb: list, Rb: list) -> np.ndarray:
+    """Diagonal of H_eff: element (q, i, j) gets c_k L[i, i] R[j, j] from every task with
+    src == dst == q (a task with src != dst has no diagonal entries).  Pinned by the diagonal of
+    heff_dense on tiny layouts."""
+    off = st.psi_offsets()
+    out = np.zeros(int(off[-1]))
+    for t, (k, s, d) in enumerate(st.tasks):
+        if s != d:
+            continue
+        blk = st.term_coef[k] * np.outer(np.diag(Lb[t]), np.diag(Rb[t]))
+        out[off[s]:off[s + 1]] += blk.reshape(-1)
+    return out
 
 
 def emulated_groups(st):

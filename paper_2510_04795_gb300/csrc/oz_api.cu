@@ -11,6 +11,7 @@
 
 #include "ozdmrg.h"
 #include "oz_gemm.cuh"
+#include "oz_internal.cuh"
 #include "oz_slice.cuh"
 
 using oz::GemmProblem;
@@ -314,6 +315,7 @@ struct oz_heff_s {
   long long nTrows = 0;
 
   double *dPsi = nullptr, *dY = nullptr;
+  double* dDiag = nullptr;  // diagonal of H_eff (Davidson preconditioner)
   bool prepared = false;
   // layout kept for the lazy per-product setup of the emulated path
   std::vector<std::vector<int>> bysrc, bydst;
@@ -437,6 +439,8 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
     oz_heff_destroy(h);
     return rc;
   };
+  if (int rc = h->alloc(&h->dDiag, (size_t)h->dim * 8)) return bail(rc);
+  if (int rc = oz::build_heff_diag(nsec, m, n, h->psioff.data(), ntask, tasks, h->dDiag)) return bail(rc);
 
   std::vector<std::vector<int>> bysrc(nsec), bydst(nsec);
   for (int t = 0; t < ntask; ++t) {
@@ -848,5 +852,22 @@ extern "C" int oz_heff_info_get(const oz_heff* h, oz_heff_info* o) {
   o->slices = h->S;
   o->level = h->s;
   o->mode = h->mode;
+  return OZ_OK;
+}
+
+// ---- library-internal hooks (oz_internal.cuh)
+namespace oz {
+int api_fail(int code, const std::string& msg) { return fail(code, msg); }
+int ctx_device(const oz_ctx* c) { return c->device; }
+long long heff_dim(const oz_heff* h) { return h->dim; }
+int heff_device(const oz_heff* h) { return h->ctx->device; }
+int heff_nsm(const oz_heff* h) { return h->ctx->nsm; }
+oz_ctx* heff_ctx(const oz_heff* h) { return h->ctx; }
+const double* heff_diag_ptr(const oz_heff* h) { return h->dDiag; }
+}  // namespace oz
+
+extern "C" int oz_heff_diag(const oz_heff* h, double* d_diag, oz_stream_t stream) {
+  if (!h || !d_diag) return fail(OZ_EINVAL, "null argument");
+  OZ_CU(cudaMemcpyAsync(d_diag, h->dDiag, (size_t)h->dim * 8, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
   return OZ_OK;
 }

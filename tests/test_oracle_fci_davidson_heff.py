@@ -80,6 +80,28 @@ def test_heff_symmetric():
     assert abs(x @ hy - hx @ y) <= 1e-13 * np.linalg.norm(hx) * np.linalg.norm(y)
 
 
+def test_heff_diag_is_diagonal_of_dense():
+    # the Davidson preconditioner: diagonal of the brute-force Kronecker sum (no other task touches it)
+    st, Lb, Rb, psi = _tiny_problem(seed=6)
+    H = heff.heff_dense(st, Lb, Rb)
+    d = heff.heff_diag(st, Lb, Rb)
+    assert np.allclose(d, np.diag(H), rtol=1e-15, atol=1e-15 * np.abs(H).max())
+    assert np.count_nonzero(d) > 0
+
+
+def test_davidson_history_and_restart():
+    # a small subspace forces restarts; the answer still matches eigh and the residuals reach tol
+    st, Lb, Rb, psi = _tiny_problem(spread=False, seed=4, grid=(3, 2), dims=(3, 8))
+    H = heff.heff_dense(st, Lb, Rb)
+    hist = []
+    theta, x, it, ok = davidson.davidson(lambda v: H @ v, np.diag(H), psi, tol=1e-9, max_sub=8, history=hist)
+    assert ok and it > 8 and len(hist) == it and hist[-1][1] <= 1e-9
+    assert abs(theta - np.linalg.eigvalsh(H)[0]) < 1e-9
+    # Ritz values of a growing or restarted Krylov-like subspace never rise (Cauchy interlacing)
+    th = [h[0] for h in hist]
+    assert all(b <= a + 1e-12 for a, b in zip(th, th[1:]))
+
+
 def test_davidson_on_dense_heff():
     st, Lb, Rb, psi = _tiny_problem(spread=False, seed=4, grid=(3, 2), dims=(3, 8))
     H = heff.heff_dense(st, Lb, Rb)
