@@ -175,6 +175,115 @@ typedef struct oz_heff_info {
 } oz_heff_info;
 int oz_heff_info_get(const oz_heff* h, oz_heff_info* out);
 
+/* Diagonal of H_eff (length dim) into d_diag: sum over the tasks with src == dst of
+ * coef L[i][i] R[j][j] at element (src, i, j) -- the Davidson preconditioner.  Built from the FP64
+ * operator blocks during oz_heff_create (an exact function of them, independent of the emulation). */
+int oz_heff_diag(const oz_heff* h, double* d_diag, oz_stream_t stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Davidson eigensolver for the lowest eigenpair of H_eff (paper, section "Theory of TNS/DMRG
+ * regarding error analysis": the two-site update solves the eigenproblem of H_eff with a Krylov
+ * method; section "Numerical procedure": stop at a residual threshold).  Iteration:
+ *   G = V^T W symmetrised, (theta, y) = lowest eigenpair of G, x = V y, r = W y - theta x;
+ *   converged when |r|_2 <= tol; otherwise d = r / (theta - diag H_eff) (|theta - diag| floored
+ *   at 1e-12, sign kept), restart to the two lowest Ritz vectors when V holds max_sub vectors,
+ *   orthogonalise d against V twice (classical Gram-Schmidt), normalise, append, W += H_eff d.
+ * Every step runs on the device in FP64 except the H_eff products (emulated or native as the handle
+ * says).  The state owns 2 (max_sub + 3) + 1 device vectors of length dim.  The handle must outlive
+ * the state.  Each davidson_step synchronises `stream` twice (it returns theta and |r|).
+ * ------------------------------------------------------------------------------------------ */
+typedef struct oz_davidson_s oz_davidson;
+/* max_sub in 3..32; tol > 0.  Errors: OZ_EINVAL, OZ_ENOMEM. */
+int oz_davidson_create(oz_heff* h, int max_sub, double tol, oz_davidson** out);
+int oz_davidson_destroy(oz_davidson* d);
+/* V = [x0 / |x0|], W = [H_eff V_0].  OZ_EINVAL if x0 has zero or non-finite norm. */
+int davidson_start(oz_davidson* d, const double* d_x0, oz_stream_t stream);
+/* One iteration: writes the Ritz value and residual norm of the current subspace; sets
+ * *converged = 1 (and expands nothing) when |r| <= tol, else expands the subspace by one vector.
+ * OZ_ENOCONV if the correction vanished after orthogonalisation (norm < 1e-14); OZ_ENONFINITE if
+ * theta or |r| is not finite. */
+int davidson_step(oz_davidson* d, double* theta, double* resid, int* converged, oz_stream_t stream);
+/* The normalised Ritz vector of the last davidson_step into d_x (length dim). */
+int davidson_ritz(oz_davidson* d, double* d_x, oz_stream_t stream);
+/* Whole solve with max_sub = 24: d_psi is the start vector on entry and the normalised Ritz vector
+ * on exit; *energy = last Ritz value, *iters = iterations.  OZ_ENOCONV when max_iter iterations did
+ * not converge (d_psi and *energy then hold the last iterate). */
+int davidson_solve(oz_heff* h, double* d_psi, double tol, int max_iter, double* energy, int* iters,
+                   oz_stream_t stream);
+/* Verification entry point of the projected eigensolver (one-CTA cyclic Jacobi, FP64): eigenvalues
+ * of the symmetric m x m matrix d_G (row-major, ldg; m in 1..32) ascending into d_w[m] and the
+ * eigenvectors as the columns of d_V (row-major m x m, ldv).  Synchronous.  OZ_ENOCONV if 60 sweeps
+ * did not bring the off-diagonal mass below 1e-32 of the total. */
+int oz_symeig_small(const double* d_G, int m, int ldg, double* d_w, double* d_V, int ldv, oz_stream_t stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Matrix product operator of the ab initio Hamiltonian (host code, no GPU needed)
+ *   H = sum_{pq,s} h_pq a+_{ps} a_{qs} + 1/2 sum_{pqrs,s,t} (pq|rs) a+_{ps} a+_{rt} a_{st} a_{qs}
+ * on L spatial orbitals, one site per orbital (local states |0>, |up>, |down>, |up down>),
+ * Jordan-Wigner order orbital-major, up before down.  It defines the renormalised operators of the
+ * two-site sweep (paper, section "Theory of TNS/DMRG ...": the effective Hamiltonian of the
+ * two-site update; the paper leaves the operator construction to the cited DMRG literature).
+ *   h1: L x L, eri: L^4 chemist-notation (pq|rs) at index ((p L + q) L + r) L + s; HOST FP64.
+ * oz_mpo_bond_dims: chi[b + 1] = number of MPO states on bond b = -1..L-1 (chi has L + 1 entries).
+ * oz_mpo_dense: the MPO contracted to the dense 4^L x 4^L matrix (row-major, basis index
+ *   sum_p s_p 4^p), for L in 2..4 -- a verification entry point.
+ * ------------------------------------------------------------------------------------------ */
+int oz_mpo_bond_dims(const double* h1, const double* eri, int L, int* chi);
+int oz_mpo_dense(const double* h1, const double* eri, int L, double* out);
+
+/* ------------------------------------------------------------------------------------------
+ * Two-site DMRG sweep (paper, section "Theory of TNS/DMRG regarding error analysis": sweep the
+ * chain; at every bond find the lowest eigenpair of the effective Hamiltonian of the two-site
+ * tensor with a Krylov method, truncate it with an SVD of the two-site tensor and renormalise the
+ * block operators; the energy approaches the exact ground state from above).
+ *   - U(1) x U(1) symmetry (electron number, 2 Sz); the environments are the MPO's partial sums
+ *     on every block, so H_eff = sum_w L_w (x) R_w is a task list of heff_apply (emulated or
+ *     native FP64 as `prec` says); its lowest eigenpair comes from davidson_solve (tolerance
+ *     davidson_tol on |r|_2, at most 1000 iterations, start vector from a counter-based generator
+ *     keyed by `seed` and the step number).
+ *   - Start: every right block holds the single state of the reference determinant (orbitals
+ *     filled from 0 with (N + 2Sz)/2 up and (N - 2Sz)/2 down electrons).
+ *   - A sweep is bonds 0..L-2 left to right, then L-2..0 right to left; every bond but the last of
+ *     a half-sweep truncates the enlarged block: all of it when it has at most D states, otherwise
+ *     the largest eigenvalues (> 1e-14, at most D, never cutting through a group of equal values)
+ *     of the reduced density matrix of each sector (FP64 on the device).
+ *   - h1 (L x L) and eri (L^4, chemist) are HOST arrays as for oz_mpo_bond_dims.
+ * Limits: a density-matrix sector may hold at most 112 states (OZ_EINVAL otherwise).
+ * Errors: OZ_EINVAL (arguments, limits), OZ_ENOCONV (Davidson or Jacobi did not converge),
+ * OZ_ENONFINITE, OZ_ECUDA, OZ_ENOMEM.  Synchronous; uses its own stream on the context's device.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct oz_dmrg_s oz_dmrg;
+typedef struct oz_dmrg_step {
+  int sweep;         /* 0-based sweep */
+  int dir;           /* 0 = left to right, 1 = right to left */
+  int bond;          /* i: the two sites are i and i + 1 */
+  int dim;           /* length of the two-site vector */
+  int nterm;         /* MPO states on the bond: terms w of H_eff */
+  int ntask;         /* sector tasks of H_eff */
+  int iters;         /* Davidson iterations */
+  int kept;          /* states of the new block (0: no truncation at this bond) */
+  double energy;     /* lowest Ritz value */
+  double discarded;  /* sum of the discarded density-matrix eigenvalues */
+} oz_dmrg_step;
+int oz_dmrg_create(oz_ctx* ctx, const double* h1, const double* eri, int L, int nelec, int twosz, int D,
+                   const oz_prec* prec, double davidson_tol, unsigned long long seed, oz_dmrg** out);
+int oz_dmrg_destroy(oz_dmrg* d);
+/* Runs nsweeps more sweeps; energies (if not null) receives 2 (L - 1) nsweeps Ritz values in
+ * bond order. */
+int oz_dmrg_run(oz_dmrg* d, int nsweeps, double* energies);
+/* Per-bond record of every step run so far (*n = count; up to cap entries copied). */
+int oz_dmrg_steps(const oz_dmrg* d, oz_dmrg_step* out, int cap, int* n);
+/* Verification entry point: builds H_eff of `bond` from the current environments; *dim = length
+ * of its two-site vector; patterns (if not null, length *dim) = determinant occupation pattern of
+ * every basis state (bit 2p = orbital p up, bit 2p + 1 down; -1 once a block was rotated by a
+ * truncation); if d_psi and d_y are not null, d_y = H_eff d_psi (device vectors).  Call first
+ * with null pointers to learn *dim. */
+int oz_dmrg_bond_heff(oz_dmrg* d, int bond, const double* d_psi, double* d_y, long long* patterns,
+                      long long* dim, oz_stream_t stream);
+/* One-shot form: create, run nsweeps, destroy. */
+int dmrg_sweep(oz_ctx* ctx, const double* h1, const double* eri, int L, int nelec, int twosz, int D, int nsweeps,
+               const oz_prec* prec, double davidson_tol, unsigned long long seed, double* energies);
+
 #ifdef __cplusplus
 }
 #endif

@@ -2,7 +2,8 @@
 
 Thin Python binding over the C ABI of libozdmrg (include/ozdmrg.h); torch supplies device
 memory and streams only.  Names follow the C ABI: ``ozaki_gemm``, ``ozaki_slice``,
-``ozaki_slice_products``, ``heff_apply`` (on an ``Heff`` handle), ``davidson_step``.
+``ozaki_slice_products``, ``heff_apply`` (on an ``Heff`` handle), ``davidson_step`` (on a
+``Davidson`` state), ``davidson_solve``, ``symeig_small``, ``dmrg_sweep`` (and the ``DMRG`` handle).
 """
 from __future__ import annotations
 
@@ -13,8 +14,9 @@ import torch
 from . import _native as N
 from ._native import OzError, OZ_MODE_EAGER, OZ_MODE_NATIVE
 
-__all__ = ["Context", "Heff", "OzError", "ozaki_gemm", "ozaki_slice", "ozaki_slice_products", "heff_apply",
-           "heff_apply_host", "heff_stage_times",
+__all__ = ["Context", "Heff", "Davidson", "OzError", "ozaki_gemm", "ozaki_slice", "ozaki_slice_products",
+           "heff_apply", "heff_apply_host", "heff_stage_times", "davidson_solve", "symeig_small", "DMRG",
+           "dmrg_sweep",
            "OZ_MODE_EAGER", "OZ_MODE_NATIVE"]
 
 
@@ -157,6 +159,49 @@ class Heff:
         N.check(self.lib.heff_apply(self.h, _ptr(psi), _ptr(y), _stream(stream)))
         return y
 
+    def diag(self, stream=None) -> torch.Tensor:
+        """Diagonal of H_eff (the Davidson preconditioner), length dim."""
+        out = torch.empty(self.dim, dtype=torch.float64, device=f"cuda:{self.ctx.device}")
+        N.check(self.lib.oz_heff_diag(self.h, _ptr(out), _stream(stream)))
+        return out
+
+
+class Davidson:
+    """Davidson state for the lowest eigenpair of an ``Heff`` (all vector work on the device)."""
+
+    def __init__(self, heff: Heff, max_sub: int = 24, tol: float = 1e-10):
+        self.heff = heff
+        self.lib = heff.lib
+        h = C.c_void_p()
+        N.check(self.lib.oz_davidson_create(heff.h, int(max_sub), float(tol), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.oz_davidson_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def start(self, x0: torch.Tensor, stream=None):
+        _check_f64(x0)
+        N.check(self.lib.davidson_start(self.h, _ptr(x0), _stream(stream)))
+
+    def step(self, stream=None):
+        """One iteration: (theta, |r|, converged).  Raises OzError(OZ_ENOCONV) on breakdown."""
+        th, rs, cv = C.c_double(), C.c_double(), C.c_int()
+        N.check(self.lib.davidson_step(self.h, C.byref(th), C.byref(rs), C.byref(cv), _stream(stream)))
+        return th.value, rs.value, bool(cv.value)
+
+    def ritz(self, stream=None) -> torch.Tensor:
+        x = torch.empty(self.heff.dim, dtype=torch.float64, device=f"cuda:{self.heff.ctx.device}")
+        N.check(self.lib.davidson_ritz(self.h, _ptr(x), _stream(stream)))
+        return x
+
 
 def heff_apply_host(h: Heff, psi_host: torch.Tensor, y_host: torch.Tensor, stream=None) -> torch.Tensor:
     """End-to-end product on host (preferably pinned) float64 tensors."""
@@ -175,3 +220,104 @@ def heff_stage_times(h: Heff) -> list:
 
 def heff_apply(h: Heff, psi: torch.Tensor, y: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     return h.apply(psi, y, stream)
+
+
+def davidson_solve(h: Heff, psi: torch.Tensor, tol: float = 1e-10, max_iter: int = 200, stream=None):
+    """Lowest eigenpair of H_eff from the start vector psi (overwritten with the Ritz vector).
+
+    Returns (energy, iterations, status) with status OZ_OK or OZ_ENOCONV; other errors raise."""
+    _check_f64(psi)
+    e, it = C.c_double(), C.c_int()
+    rc = h.lib.davidson_solve(h.h, _ptr(psi), float(tol), int(max_iter), C.byref(e), C.byref(it), _stream(stream))
+    if rc not in (N.OZ_OK, N.OZ_ENOCONV):
+        N.check(rc)
+    return e.value, it.value, rc
+
+
+def symeig_small(G: torch.Tensor, stream=None):
+    """(eigenvalues ascending, eigenvectors as columns) of a symmetric m x m CUDA float64 matrix, m <= 32."""
+    _check_f64(G)
+    m = G.shape[0]
+    w = torch.empty(m, dtype=torch.float64, device=G.device)
+    V = torch.empty(m, m, dtype=torch.float64, device=G.device)
+    N.check(N.load().oz_symeig_small(_ptr(G), m, G.stride(0), _ptr(w), _ptr(V), m, _stream(stream)))
+    return w, V
+
+
+def _host_integrals(h1, eri):
+    import numpy as np
+    h1 = np.ascontiguousarray(np.asarray(h1, dtype=np.float64))
+    eri = np.ascontiguousarray(np.asarray(eri, dtype=np.float64))
+    L = h1.shape[0]
+    if h1.shape != (L, L) or eri.size != L ** 4:
+        raise OzError(N.OZ_EINVAL, "h1 must be L x L and eri L^4")
+    return h1, eri, L
+
+
+class DMRG:
+    """Two-site DMRG of the ab initio Hamiltonian (h1, eri host arrays, chemist notation)."""
+
+    def __init__(self, ctx: Context, h1, eri, nelec: int, twosz: int, D: int, slices=7, level=0, mode="eager",
+                 tol: float = 1e-10, seed: int = 0):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        self._h1, self._eri, self.L = _host_integrals(h1, eri)
+        p = _prec(slices, level, mode)
+        h = C.c_void_p()
+        N.check(self.lib.oz_dmrg_create(ctx.h, self._h1.ctypes.data, self._eri.ctypes.data, self.L, int(nelec),
+                                        int(twosz), int(D), C.byref(p), float(tol), int(seed), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.oz_dmrg_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, nsweeps: int):
+        """Runs nsweeps sweeps; returns the 2 (L - 1) nsweeps bond energies."""
+        import numpy as np
+        e = np.zeros(max(1, 2 * (self.L - 1) * nsweeps))
+        N.check(self.lib.oz_dmrg_run(self.h, int(nsweeps), e.ctypes.data))
+        return e[: 2 * (self.L - 1) * nsweeps]
+
+    def steps(self) -> list:
+        n = C.c_int()
+        N.check(self.lib.oz_dmrg_steps(self.h, None, 0, C.byref(n)))
+        arr = (N.oz_dmrg_step * max(1, n.value))()
+        N.check(self.lib.oz_dmrg_steps(self.h, arr, n.value, C.byref(n)))
+        return [{f: getattr(arr[i], f) for f, _ in N.oz_dmrg_step._fields_} for i in range(n.value)]
+
+    def bond_heff(self, bond: int, psi: torch.Tensor | None = None, stream=None):
+        """(H_eff psi or None, determinant pattern of every two-site basis state) at a bond."""
+        import numpy as np
+        dim = C.c_longlong()
+        N.check(self.lib.oz_dmrg_bond_heff(self.h, int(bond), None, None, None, C.byref(dim), _stream(stream)))
+        pats = np.zeros(dim.value, dtype=np.int64)
+        y = None
+        if psi is not None:
+            _check_f64(psi)
+            if psi.numel() != dim.value:
+                raise OzError(N.OZ_EINVAL, "psi has the wrong length")
+            y = torch.empty_like(psi)
+        N.check(self.lib.oz_dmrg_bond_heff(self.h, int(bond), _ptr(psi) if psi is not None else None,
+                                           _ptr(y) if y is not None else None, pats.ctypes.data, C.byref(dim),
+                                           _stream(stream)))
+        return y, pats
+
+
+def dmrg_sweep(ctx: Context, h1, eri, nelec: int, twosz: int, D: int, nsweeps: int, slices=7, level=0,
+               mode="eager", tol: float = 1e-10, seed: int = 0):
+    """One-shot sweep run; returns the 2 (L - 1) nsweeps bond energies."""
+    import numpy as np
+    h1, eri, L = _host_integrals(h1, eri)
+    p = _prec(slices, level, mode)
+    e = np.zeros(max(1, 2 * (L - 1) * nsweeps))
+    N.check(ctx.lib.dmrg_sweep(ctx.h, h1.ctypes.data, eri.ctypes.data, L, int(nelec), int(twosz), int(D),
+                               int(nsweeps), C.byref(p), float(tol), int(seed), e.ctypes.data))
+    return e[: 2 * (L - 1) * nsweeps]

@@ -36,12 +36,10 @@ class oz_heff_info(C.Structure):
                 ("gemm2_tiles", C.c_longlong), ("slices", C.c_int), ("level", C.c_int), ("mode", C.c_int)]
 
 
-class oz_davidson_opts(C.Structure):
-    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("max_sub", C.c_int)]
-
-
-class oz_davidson_result(C.Structure):
-    _fields_ = [("theta", C.c_double), ("resid", C.c_double), ("iters", C.c_int), ("converged", C.c_int)]
+class oz_dmrg_step(C.Structure):
+    _fields_ = [("sweep", C.c_int), ("dir", C.c_int), ("bond", C.c_int), ("dim", C.c_int), ("nterm", C.c_int),
+                ("ntask", C.c_int), ("iters", C.c_int), ("kept", C.c_int), ("energy", C.c_double),
+                ("discarded", C.c_double)]
 
 
 _lib = None
@@ -77,12 +75,23 @@ def load():
         "heff_apply_host": (i, [vp, vp, vp, vp]),
         "oz_heff_stage_times": (i, [vp, C.POINTER(C.c_float)]),
         "oz_heff_diag": (i, [vp, vp, vp]),
-        "davidson_step": (i, [vp, vp, vp, C.POINTER(oz_davidson_result), vp]),
-        "davidson_solve": (i, [vp, vp, C.POINTER(oz_davidson_opts), C.POINTER(oz_davidson_result), vp]),
+        "oz_davidson_create": (i, [vp, i, d, C.POINTER(vp)]),
+        "oz_davidson_destroy": (i, [vp]),
+        "davidson_start": (i, [vp, vp, vp]),
+        "davidson_step": (i, [vp, C.POINTER(d), C.POINTER(d), C.POINTER(i), vp]),
+        "davidson_ritz": (i, [vp, vp, vp]),
+        "davidson_solve": (i, [vp, vp, d, i, C.POINTER(d), C.POINTER(i), vp]),
+        "oz_symeig_small": (i, [vp, i, i, vp, vp, i, vp]),
+        "oz_mpo_bond_dims": (i, [vp, vp, i, vp]),
+        "oz_mpo_dense": (i, [vp, vp, i, vp]),
+        "oz_dmrg_create": (i, [vp, vp, vp, i, i, i, i, C.POINTER(oz_prec), d, C.c_ulonglong, C.POINTER(vp)]),
+        "oz_dmrg_destroy": (i, [vp]),
+        "oz_dmrg_run": (i, [vp, i, vp]),
+        "oz_dmrg_steps": (i, [vp, vp, i, C.POINTER(i)]),
+        "oz_dmrg_bond_heff": (i, [vp, i, vp, vp, vp, C.POINTER(ll), vp]),
+        "dmrg_sweep": (i, [vp, vp, vp, i, i, i, i, i, C.POINTER(oz_prec), d, C.c_ulonglong, vp]),
     }
     for name, (res, args) in sig.items():
-        if not hasattr(L, name):
-            continue
         f = getattr(L, name)
         f.restype = res
         f.argtypes = args

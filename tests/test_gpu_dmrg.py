@@ -1,0 +1,93 @@
+"""GPU two-site DMRG (dmrg_sweep, oz_dmrg_*) against the explicit-basis oracle and FCI."""
+import numpy as np
+import pytest
+import torch
+
+import synthetic
+from oracle import dmrg as odmrg
+from oracle import fci
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2510_04795_gb300 as oz
+    c = oz.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("mode,tol", [("eager", 1e-12), ("native", 1e-13)])
+def test_bond_heff_is_projected_fci_hamiltonian(ctx, mode, tol):
+    """Without truncation every block basis is a set of determinants, and H_eff of every bond
+    must be the FCI Hamiltonian restricted to the bond's two-site basis (P^T H P)."""
+    import paper_2510_04795_gb300 as oz
+    L, N, twosz = 6, 6, 0
+    h, eri = synthetic.integrals(L, seed=0)
+    H, pats_fci = odmrg.orbital_major_hamiltonian(h, eri, N, twosz)
+    index = {int(p): i for i, p in enumerate(pats_fci)}
+    d = oz.DMRG(ctx, h, eri, N, twosz, D=4096, mode=mode)
+    d.run(1)
+    rng = np.random.default_rng(1)
+    for bond in range(L - 1):
+        _, pats = d.bond_heff(bond)
+        assert np.all(pats >= 0) and len(set(pats.tolist())) == len(pats)
+        idx = np.array([index[int(p)] for p in pats])
+        x = rng.normal(size=len(pats))
+        y, _ = d.bond_heff(bond, torch.from_numpy(x).cuda())
+        ref = H[idx][:, idx] @ x
+        err = np.linalg.norm(y.cpu().numpy() - ref) / np.linalg.norm(ref)
+        assert err <= tol, (bond, err)
+    d.close()
+
+
+def test_sweep_c0_matches_oracle_and_fci(ctx):
+    """L = N = 8 (the 4900-determinant sector), D = 64, S = 7: every bond energy of every sweep
+    agrees with the explicit-basis oracle, stays above FCI and is exact at the middle bond."""
+    import paper_2510_04795_gb300 as oz
+    L, N, D, nsw = 8, 8, 64, 4
+    h, eri = synthetic.integrals(L, seed=0)
+    e_fci = fci.ground_state(h, eri, N, 0)[0]
+    got = oz.dmrg_sweep(ctx, h, eri, N, 0, D, nsw, slices=7)
+    ref = np.array(odmrg.ExplicitDMRG(h, eri, N, 0, D).sweep(nsw))
+    assert np.max(np.abs(got - ref)) <= 1e-6
+    assert np.all(got >= e_fci - 1e-10)
+    E = got.reshape(nsw, 2, L - 1)
+    assert abs(E[-1, 0, 3] - e_fci) <= 1e-9          # the middle bond spans the whole sector
+    assert np.all(np.diff(E[:, 1, -1]) <= 1e-10)      # end-of-sweep energy never rises
+
+
+def test_sweep_without_truncation_reaches_fci(ctx):
+    import paper_2510_04795_gb300 as oz
+    L, N = 8, 8
+    h, eri = synthetic.integrals(L, seed=0)
+    e_fci = fci.ground_state(h, eri, N, 0)[0]
+    d = oz.DMRG(ctx, h, eri, N, 0, D=256, slices=7)
+    E = d.run(2).reshape(2, 2, L - 1)
+    assert np.all(np.abs(E[1] - e_fci) <= 1e-9)
+    st = d.steps()
+    assert all(s["iters"] > 0 for s in st)
+    assert max(s["nterm"] for s in st) > 100
+    d.close()
+
+
+def test_sweep_native_and_emulated_agree(ctx):
+    import paper_2510_04795_gb300 as oz
+    L, N = 6, 6
+    h, eri = synthetic.integrals(L, seed=2)
+    a = oz.dmrg_sweep(ctx, h, eri, N, 0, 16, 2, slices=7)
+    b = oz.dmrg_sweep(ctx, h, eri, N, 0, 16, 2, mode="native")
+    assert np.max(np.abs(a - b)) <= 1e-8
+
+
+def test_sweep_rejects_bad_arguments(ctx):
+    import paper_2510_04795_gb300 as oz
+    from paper_2510_04795_gb300 import OzError
+    h, eri = synthetic.integrals(4, seed=0)
+    with pytest.raises(OzError):
+        oz.dmrg_sweep(ctx, h, eri, 9, 0, 16, 1)       # more electrons than spin orbitals
+    with pytest.raises(OzError):
+        oz.dmrg_sweep(ctx, h, eri, 4, 1, 16, 1)       # parity of N and 2Sz differ
+    with pytest.raises(OzError):
+        oz.dmrg_sweep(ctx, h, eri, 4, 0, 0, 1)        # D = 0
