@@ -174,6 +174,70 @@ typedef struct oz_heff_info {
   int slices, level, mode;
 } oz_heff_info;
 int oz_heff_info_get(const oz_heff* h, oz_heff_info* out);
+/* Per-block precision dial (emulated handles): s1[q] = slice level of the stage-1 product of
+ * source sector q, s2[q] = level of the stage-2 product of target sector q (arrays of nsec ints;
+ * null = the handle's level).  Each level must lie in 1..the handle's level s; the operator and
+ * psi digits stay S deep and a product at level t uses digits 1..t and the pairs t+u <= t+1 of
+ * the header comment.  Takes effect for the next product (the problem tables are rewritten in
+ * place; synchronises the device).  info.carrier_flops follows the levels. */
+int oz_heff_set_levels(oz_heff* h, const int* s1, const int* s2);
+int oz_heff_get_levels(const oz_heff* h, int* s1, int* s2);
+
+/* ------------------------------------------------------------------------------------------
+ * Slice-level selection per block (the precision dial of sections "Theory of emulated FP64
+ * arithmetic" and "Numerical procedure"; the paper's library picks the slice count per GEMM).
+ *
+ * Features of one product (OZ_NFEAT floats): for A (rows) then B (columns), the fractions of
+ * elements whose exponent lies 0, 1, 2-3, 4-7, 8-15, 16-31, 32-63, >= 64 below the largest of
+ * their row/column, and the fraction of zeros (9 + 9); then log2(K)/16 and log2(M N)/32.
+ * oz_heff_problem_features: features of every stage-1 product (feat1, row q = source sector q)
+ *   and stage-2 product (feat2, row q = target sector q) for psi (rows of sectors without a
+ *   product are zero); runs one product at the handle's level.  Host arrays of nsec x OZ_NFEAT.
+ * oz_heff_problem_errors: true relative Frobenius errors of every product at `level` against the
+ *   handle's own level (stage 1 with stage 2 at the full level and vice versa); err = -1 where a
+ *   sector has no product.  Host arrays of nsec.  Levels are restored afterwards.
+ * oz_heff_select_levels: picks and sets per-product levels with the smallest carrier flops it can
+ *   reach greedily while the predicted error of each stage output, sum_q (10^(pred_q + margin)
+ *   |out_q|)^2, stays within (budget |out| / sqrt 2)^2 (norms from one product at the full level;
+ *   `budget` is a relative Frobenius error, `margin` a safety in decades).  selector:
+ *   OZ_SELECT_FIXED (the handle's level), OZ_SELECT_ANALYTIC (error 2^(gA + gB - 8 s + 3) from
+ *   the effective exponent gaps), OZ_SELECT_LEARNED (`net`, OZ_NFEAT inputs, outputs = log10
+ *   error at levels 3..8).  Levels below 3 are never picked.  Writes the levels to s1/s2 (may be
+ *   null).
+ * ------------------------------------------------------------------------------------------ */
+#define OZ_NFEAT 20
+#define OZ_SELECT_FIXED 0
+#define OZ_SELECT_ANALYTIC 1
+#define OZ_SELECT_LEARNED 2
+typedef struct oz_mlp_s oz_mlp;
+int oz_heff_problem_features(oz_heff* h, const double* d_psi, float* feat1, float* feat2, oz_stream_t stream);
+int oz_heff_problem_errors(oz_heff* h, const double* d_psi, int level, double* err1, double* err2,
+                           oz_stream_t stream);
+int oz_heff_select_levels(oz_heff* h, const double* d_psi, int selector, double budget, oz_mlp* net, double margin,
+                          int* s1, int* s2, oz_stream_t stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Selector network: a two-hidden-layer tanh MLP in FP32, trained on the device by its own
+ * forward, backward and Adam kernels.  H1 = tanh(X W1 + b1), H2 = tanh(H1 W2 + b2),
+ * Y = H2 W3 + b3; loss = sum(M (Y - T)^2) / max(1, sum M) (M masks missing targets).  Parameters
+ * flattened as W1 (nin x nh, row-major), b1, W2, b2, W3, b3; Xavier-uniform init from `seed`.
+ * Device matrices are row-major FP32 (X: rows x nin; Y, T, M: rows x nout).
+ * oz_mlp_gradient: loss and gradient over all rows (host_grad: param_count floats, may be null).
+ * oz_mlp_train: epochs of Adam (b1 0.9, b2 0.999, eps 1e-8) over shuffled minibatches of
+ *   `batch` rows (a partial last batch is skipped); final_loss (may be null) = loss over all rows.
+ * ------------------------------------------------------------------------------------------ */
+int oz_mlp_create(int nin, int nhidden, int nout, unsigned long long seed, oz_mlp** out);
+int oz_mlp_destroy(oz_mlp* net);
+int oz_mlp_param_count(const oz_mlp* net);
+int oz_mlp_nin(const oz_mlp* net);
+int oz_mlp_nout(const oz_mlp* net);
+int oz_mlp_get_params(const oz_mlp* net, float* host);
+int oz_mlp_set_params(oz_mlp* net, const float* host);
+int oz_mlp_forward(oz_mlp* net, const float* d_X, int rows, float* d_Y, oz_stream_t stream);
+int oz_mlp_gradient(oz_mlp* net, const float* d_X, const float* d_T, const float* d_M, int rows, float* loss,
+                    float* host_grad, oz_stream_t stream);
+int oz_mlp_train(oz_mlp* net, const float* d_X, const float* d_T, const float* d_M, int rows, int epochs, int batch,
+                 float lr, unsigned long long seed, float* final_loss, oz_stream_t stream);
 
 /* Diagonal of H_eff (length dim) into d_diag: sum over the tasks with src == dst of
  * coef L[i][i] R[j][j] at element (src, i, j) -- the Davidson preconditioner.  Built from the FP64

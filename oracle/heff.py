@@ -88,14 +88,20 @@ def emulated_groups(st):
     return by_src, by_dst
 
 
-def heff_apply_emulated(st, Lb: list, Rb: list, psi_flat, S: int, s: int | None = None) -> np.ndarray:
+def heff_apply_emulated(st, Lb: list, Rb: list, psi_flat, S: int, s: int | None = None, s1=None,
+                        s2=None) -> np.ndarray:
     """Two-stage emulated H_eff psi.
 
     Stage 1 (per source q): T = ozaki([L_t1; L_t2; ...], psi[q]) -> T_t blocks.
     Stage 2 (per target q'): Y[q'] = ozaki([T_t1 T_t2 ...], [(c R_t1)^T; (c R_t2)^T; ...]),
     where c R is rounded to FP64 first.  Both are one emulated DGEMM each (shared row
     exponents of the concatenated rows, shared column exponents of the stacked columns).
+    Slice levels: s for every product, or per sector -- s1[q] for the stage-1 product of source
+    sector q and s2[q] for the stage-2 product of target sector q (the precision dial per block).
     """
+    s = S if s is None else s
+    s1 = [s] * st.nsec if s1 is None else list(s1)
+    s2 = [s] * st.nsec if s2 is None else list(s2)
     P = _blocks(psi_flat, st)
     by_src, by_dst = emulated_groups(st)
     T = [None] * st.ntask
@@ -104,7 +110,7 @@ def heff_apply_emulated(st, Lb: list, Rb: list, psi_flat, S: int, s: int | None 
         if not ts:
             continue
         A1 = np.vstack([Lb[t] for t in ts])
-        C1 = ozaki.ozaki_gemm(A1, P[q], S, s)
+        C1 = ozaki.ozaki_gemm(A1, P[q], S, s1[q])
         r = 0
         for t in ts:
             h = Lb[t].shape[0]
@@ -118,7 +124,7 @@ def heff_apply_emulated(st, Lb: list, Rb: list, psi_flat, S: int, s: int | None 
             continue
         A2 = np.hstack([T[t] for t in ts])
         B2 = np.vstack([(st.term_coef[st.tasks[t][0]] * Rb[t]).T for t in ts])
-        Y.append(ozaki.ozaki_gemm(A2, B2, S, s))
+        Y.append(ozaki.ozaki_gemm(A2, B2, S, s2[q]))
     return _flat(Y)
 
 

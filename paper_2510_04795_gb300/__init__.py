@@ -3,7 +3,8 @@
 Thin Python binding over the C ABI of libozdmrg (include/ozdmrg.h); torch supplies device
 memory and streams only.  Names follow the C ABI: ``ozaki_gemm``, ``ozaki_slice``,
 ``ozaki_slice_products``, ``heff_apply`` (on an ``Heff`` handle), ``davidson_step`` (on a
-``Davidson`` state), ``davidson_solve``, ``symeig_small``, ``dmrg_sweep`` (and the ``DMRG`` handle).
+``Davidson`` state), ``davidson_solve``, ``symeig_small``, ``dmrg_sweep`` (and the ``DMRG`` handle), the
+per-block precision dial (``Heff.set_levels``, ``Heff.select_levels``) and the selector network ``MLP``.
 """
 from __future__ import annotations
 
@@ -12,11 +13,13 @@ import ctypes as C
 import torch
 
 from . import _native as N
-from ._native import OzError, OZ_MODE_EAGER, OZ_MODE_NATIVE
+from ._native import OzError, OZ_MODE_EAGER, OZ_MODE_NATIVE, OZ_NFEAT
+
+SELECTORS = {"fixed": N.OZ_SELECT_FIXED, "analytic": N.OZ_SELECT_ANALYTIC, "learned": N.OZ_SELECT_LEARNED}
 
 __all__ = ["Context", "Heff", "Davidson", "OzError", "ozaki_gemm", "ozaki_slice", "ozaki_slice_products",
            "heff_apply", "heff_apply_host", "heff_stage_times", "davidson_solve", "symeig_small", "DMRG",
-           "dmrg_sweep",
+           "dmrg_sweep", "MLP", "OZ_NFEAT", "SELECTORS",
            "OZ_MODE_EAGER", "OZ_MODE_NATIVE"]
 
 
@@ -158,6 +161,53 @@ class Heff:
             y = torch.empty_like(psi)
         N.check(self.lib.heff_apply(self.h, _ptr(psi), _ptr(y), _stream(stream)))
         return y
+
+    def set_levels(self, s1=None, s2=None):
+        """Per-sector slice levels: s1[q] for the stage-1 product of source sector q, s2[q] for the
+        stage-2 product of target sector q (None = the handle's level)."""
+        nsec = len(self.m)
+        a = (C.c_int * nsec)(*[int(x) for x in s1]) if s1 is not None else None
+        b = (C.c_int * nsec)(*[int(x) for x in s2]) if s2 is not None else None
+        N.check(self.lib.oz_heff_set_levels(self.h, a, b))
+
+    def get_levels(self):
+        nsec = len(self.m)
+        a, b = (C.c_int * nsec)(), (C.c_int * nsec)()
+        N.check(self.lib.oz_heff_get_levels(self.h, a, b))
+        return list(a), list(b)
+
+    def problem_features(self, psi: torch.Tensor, stream=None):
+        """(feat1, feat2): nsec x OZ_NFEAT float32 numpy arrays of the stage-1 / stage-2 products."""
+        import numpy as np
+        _check_f64(psi)
+        nsec = len(self.m)
+        f1 = np.zeros((nsec, OZ_NFEAT), dtype=np.float32)
+        f2 = np.zeros((nsec, OZ_NFEAT), dtype=np.float32)
+        N.check(self.lib.oz_heff_problem_features(self.h, _ptr(psi), f1.ctypes.data, f2.ctypes.data,
+                                                  _stream(stream)))
+        return f1, f2
+
+    def problem_errors(self, psi: torch.Tensor, level: int, stream=None):
+        """(err1, err2): relative errors of every product at `level` against the handle's level."""
+        import numpy as np
+        _check_f64(psi)
+        nsec = len(self.m)
+        e1, e2 = np.zeros(nsec), np.zeros(nsec)
+        N.check(self.lib.oz_heff_problem_errors(self.h, _ptr(psi), int(level), e1.ctypes.data, e2.ctypes.data,
+                                                _stream(stream)))
+        return e1, e2
+
+    def select_levels(self, psi: torch.Tensor, selector="learned", budget=1e-12, net=None, margin=0.5,
+                      stream=None):
+        """Pick and set per-product levels (see oz_heff_select_levels); returns (s1, s2)."""
+        _check_f64(psi)
+        nsec = len(self.m)
+        a, b = (C.c_int * nsec)(), (C.c_int * nsec)()
+        sel = SELECTORS.get(selector, selector)
+        N.check(self.lib.oz_heff_select_levels(self.h, _ptr(psi), int(sel), float(budget),
+                                               net.h if net is not None else None, float(margin), a, b,
+                                               _stream(stream)))
+        return list(a), list(b)
 
     def diag(self, stream=None) -> torch.Tensor:
         """Diagonal of H_eff (the Davidson preconditioner), length dim."""
@@ -321,3 +371,57 @@ def dmrg_sweep(ctx: Context, h1, eri, nelec: int, twosz: int, D: int, nsweeps: i
     N.check(ctx.lib.dmrg_sweep(ctx.h, h1.ctypes.data, eri.ctypes.data, L, int(nelec), int(twosz), int(D),
                                int(nsweeps), C.byref(p), float(tol), int(seed), e.ctypes.data))
     return e[: 2 * (L - 1) * nsweeps]
+
+
+class MLP:
+    """Selector network (two tanh hidden layers, FP32) trained on the device by its own kernels."""
+
+    def __init__(self, nin: int = OZ_NFEAT, nhidden: int = 64, nout: int = 6, seed: int = 4):
+        self.lib = N.load()
+        h = C.c_void_p()
+        N.check(self.lib.oz_mlp_create(int(nin), int(nhidden), int(nout), int(seed), C.byref(h)))
+        self.h = h
+        self.nin, self.nhidden, self.nout = nin, nhidden, nout
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.oz_mlp_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        import numpy as np
+        out = np.zeros(self.lib.oz_mlp_param_count(self.h), dtype=np.float32)
+        N.check(self.lib.oz_mlp_get_params(self.h, out.ctypes.data))
+        return out
+
+    def set_params(self, flat):
+        import numpy as np
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        N.check(self.lib.oz_mlp_set_params(self.h, flat.ctypes.data))
+
+    def forward(self, X: torch.Tensor, stream=None) -> torch.Tensor:
+        X = X.contiguous()
+        Y = torch.empty(X.shape[0], self.nout, dtype=torch.float32, device=X.device)
+        N.check(self.lib.oz_mlp_forward(self.h, _ptr(X), X.shape[0], _ptr(Y), _stream(stream)))
+        return Y
+
+    def gradient(self, X, T, M, stream=None):
+        """(loss, flat gradient) over all rows."""
+        import numpy as np
+        g = np.zeros(self.lib.oz_mlp_param_count(self.h), dtype=np.float32)
+        loss = C.c_float()
+        N.check(self.lib.oz_mlp_gradient(self.h, _ptr(X), _ptr(T), _ptr(M), X.shape[0], C.byref(loss), g.ctypes.data,
+                                         _stream(stream)))
+        return loss.value, g
+
+    def train(self, X, T, M, epochs=200, batch=64, lr=1e-3, seed=5, stream=None) -> float:
+        loss = C.c_float()
+        N.check(self.lib.oz_mlp_train(self.h, _ptr(X), _ptr(T), _ptr(M), X.shape[0], int(epochs), int(batch),
+                                      float(lr), int(seed), C.byref(loss), _stream(stream)))
+        return loss.value

@@ -12,6 +12,8 @@ _LIBPATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "lib
 
 OZ_OK, OZ_EINVAL, OZ_ENONFINITE, OZ_ENOCONV, OZ_EVARIATIONAL, OZ_ETIMEOUT, OZ_ECUDA, OZ_ENOMEM = range(8)
 OZ_MODE_EAGER, OZ_MODE_NATIVE = 0, 1
+OZ_NFEAT = 20
+OZ_SELECT_FIXED, OZ_SELECT_ANALYTIC, OZ_SELECT_LEARNED = 0, 1, 2
 STATUS_NAMES = {0: "OZ_OK", 1: "OZ_EINVAL", 2: "OZ_ENONFINITE", 3: "OZ_ENOCONV", 4: "OZ_EVARIATIONAL",
                 5: "OZ_ETIMEOUT", 6: "OZ_ECUDA", 7: "OZ_ENOMEM"}
 
@@ -75,6 +77,21 @@ def load():
         "heff_apply_host": (i, [vp, vp, vp, vp]),
         "oz_heff_stage_times": (i, [vp, C.POINTER(C.c_float)]),
         "oz_heff_diag": (i, [vp, vp, vp]),
+        "oz_heff_set_levels": (i, [vp, vp, vp]),
+        "oz_heff_problem_features": (i, [vp, vp, vp, vp, vp]),
+        "oz_heff_problem_errors": (i, [vp, vp, i, vp, vp, vp]),
+        "oz_heff_select_levels": (i, [vp, vp, i, d, vp, d, vp, vp, vp]),
+        "oz_mlp_create": (i, [i, i, i, C.c_ulonglong, C.POINTER(vp)]),
+        "oz_mlp_destroy": (i, [vp]),
+        "oz_mlp_param_count": (i, [vp]),
+        "oz_mlp_nin": (i, [vp]),
+        "oz_mlp_nout": (i, [vp]),
+        "oz_mlp_get_params": (i, [vp, vp]),
+        "oz_mlp_set_params": (i, [vp, vp]),
+        "oz_mlp_forward": (i, [vp, vp, i, vp, vp]),
+        "oz_mlp_gradient": (i, [vp, vp, vp, vp, i, C.POINTER(C.c_float), vp, vp]),
+        "oz_mlp_train": (i, [vp, vp, vp, vp, i, i, i, C.c_float, C.c_ulonglong, C.POINTER(C.c_float), vp]),
+        "oz_heff_get_levels": (i, [vp, vp, vp]),
         "oz_davidson_create": (i, [vp, i, d, C.POINTER(vp)]),
         "oz_davidson_destroy": (i, [vp]),
         "davidson_start": (i, [vp, vp, vp]),

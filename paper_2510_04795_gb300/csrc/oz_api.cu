@@ -11,6 +11,7 @@
 
 #include "ozdmrg.h"
 #include "oz_gemm.cuh"
+#include "oz_handles.cuh"
 #include "oz_internal.cuh"
 #include "oz_slice.cuh"
 
@@ -66,30 +67,6 @@ __global__ void fill_int_kernel(int* p, long long n, int v) {
 }
 }  // namespace
 
-struct oz_ctx_s {
-  int device = 0;
-  int nsm = 0;
-  char* ws = nullptr;
-  size_t ws_bytes = 0;
-  int* d_flags = nullptr;  // [0] non-finite input, [1] kernel timeout/abort
-  cublasHandle_t cublas = nullptr;
-
-  // bump allocation inside the workspace (grown with cudaMalloc when too small)
-  int reserve(size_t bytes) {
-    if (bytes <= ws_bytes) return OZ_OK;
-    if (ws) {
-      cudaDeviceSynchronize();
-      cudaFree(ws);
-      ws = nullptr;
-      ws_bytes = 0;
-    }
-    size_t b = std::max(bytes, (size_t)64 << 20);
-    cudaError_t e = cudaMalloc(&ws, b);
-    if (e != cudaSuccess) return cuda_fail(e, "workspace cudaMalloc");
-    ws_bytes = b;
-    return OZ_OK;
-  }
-};
 
 extern "C" const char* oz_last_error(void) { return g_err.c_str(); }
 
@@ -283,62 +260,6 @@ extern "C" int ozaki_slice_products(oz_ctx* c, int m, int n, int k, const double
 // --------------------------------------------------------------------------------------------
 // H_eff handle
 // --------------------------------------------------------------------------------------------
-struct oz_heff_s {
-  oz_ctx* ctx = nullptr;
-  int nsec = 0, ntask = 0, S = 7, s = 7, mode = OZ_MODE_EAGER;
-  std::vector<int> m, n;
-  std::vector<long long> psioff;
-  long long dim = 0, flops = 0, carrier_flops = 0, bytes_ops = 0, bytes_scratch = 0;
-  std::vector<void*> allocs;
-
-  // emulated path
-  __half *dA1 = nullptr, *dB1 = nullptr, *dA2 = nullptr, *dB2 = nullptr;
-  double* dStage = nullptr;
-  int *eB1 = nullptr, *eA2 = nullptr;
-  unsigned long long *mB1 = nullptr, *mA2 = nullptr;
-  size_t bytes_mB1 = 0, bytes_mA2 = 0;
-  GemmProblem *dP1 = nullptr, *dP2 = nullptr;
-  GemmTile *dT1 = nullptr, *dT2 = nullptr;
-  int nt1 = 0, nt2 = 0;
-  SliceSeg *dSegPsi = nullptr, *dSegA2 = nullptr;
-  int nsegPsi = 0, nsegA2 = 0;
-  long long uPsiM = 0, uPsiD = 0, uA2D = 0;
-  bool zero_y = false;
-
-  // native path (stacked FP64 copies)
-  double *nA1 = nullptr, *nB2 = nullptr, *nT = nullptr;
-  struct NatG1 { long long a1off, toff; int rows, kdim, q; };
-  struct NatG2 { long long stoff, b2off; int q, ld2; };
-  std::vector<NatG1> nat1;
-  std::vector<NatG2> nat2;
-  long long* dScatter = nullptr;  // per stacked T row: destination offset in the staging buffer
-  long long nTrows = 0;
-
-  double *dPsi = nullptr, *dY = nullptr;
-  double* dDiag = nullptr;  // diagonal of H_eff (Davidson preconditioner)
-  bool prepared = false;
-  // layout kept for the lazy per-product setup of the emulated path
-  std::vector<std::vector<int>> bysrc, bydst;
-  std::vector<int> rows1, nkb1, nkb2, ld2, tsrc, tdst;
-  std::vector<long long> offk, rowin1, stoff, A1off, B1off, A2off, B2off, A1row, B1row, A2row, B2row;
-  int* eA1 = nullptr;
-  int* eB2 = nullptr;
-  int prepare();
-  cudaStream_t cap = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // stage boundaries of the last product
-
-  template <class T>
-  int alloc(T** p, size_t bytes) {
-    *p = nullptr;
-    if (bytes == 0) bytes = 256;
-    cudaError_t e = cudaMalloc((void**)p, bytes);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-    allocs.push_back((void*)*p);
-    return OZ_OK;
-  }
-  int enqueue(cudaStream_t st, bool capturing = false);
-};
 
 namespace {
 __global__ void scatter_rows_kernel(const double* __restrict__ T, const long long* __restrict__ rowinfo,
@@ -397,6 +318,24 @@ int oz_heff_s::enqueue(cudaStream_t st, bool capturing) {
 }
 
 namespace {
+// Tensor-core flops of one emulated product (padded tiles included) at the given levels.
+long long carrier_flops_of(int nsec, const int* m, const int* n, const std::vector<int>& rows1,
+                           const std::vector<int>& nkb1, const std::vector<int>& nkb2,
+                           const std::vector<std::vector<int>>& bysrc, const std::vector<std::vector<int>>& bydst,
+                           const std::vector<int>& lev1, const std::vector<int>& lev2) {
+  long long f = 0;
+  for (int q = 0; q < nsec; ++q) {
+    const long long P1 = (long long)lev1[q] * (lev1[q] + 1) / 2, P2 = (long long)lev2[q] * (lev2[q] + 1) / 2;
+    if (!bysrc[q].empty())
+      f += P1 * 2 * (cdiv(rows1[q], oz::TILE_M) * oz::TILE_M) * (cdiv(n[q], oz::BN) * oz::BN) *
+           ((long long)nkb1[q] * oz::KB);
+    if (!bydst[q].empty())
+      f += P2 * 2 * (cdiv(m[q], oz::TILE_M) * oz::TILE_M) * (cdiv(n[q], oz::BN) * oz::BN) *
+           ((long long)nkb2[q] * oz::KB);
+  }
+  return f;
+}
+
 __global__ void copy_block_kernel(const double* __restrict__ src, int rows, int cols, long long lds, double scale,
                                   double* __restrict__ dst, long long ldd) {
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -432,6 +371,8 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
   h->mode = mode;
   h->m.assign(m, m + nsec);
   h->n.assign(n, n + nsec);
+  h->lev1.assign(nsec, s);
+  h->lev2.assign(nsec, s);
   h->psioff.assign(nsec + 1, 0);
   for (int q = 0; q < nsec; ++q) h->psioff[q + 1] = h->psioff[q] + (long long)m[q] * n[q];
   h->dim = h->psioff[nsec];
@@ -487,14 +428,7 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
     A2row[q + 1] = A2row[q] + nrbA2 * oz::TILE_M;
     B2row[q + 1] = B2row[q] + nrbB2 * oz::BN;
   }
-  const long long P1 = (long long)s * (s + 1) / 2;
-  for (int q = 0; q < nsec; ++q) {
-    h->carrier_flops += P1 * 2 * (cdiv(rows1[q], oz::TILE_M) * oz::TILE_M) * (cdiv(n[q], oz::BN) * oz::BN) *
-                        ((long long)nkb1[q] * oz::KB);
-    if (!bydst[q].empty())
-      h->carrier_flops += P1 * 2 * (cdiv(m[q], oz::TILE_M) * oz::TILE_M) * (cdiv(n[q], oz::BN) * oz::BN) *
-                          ((long long)nkb2[q] * oz::KB);
-  }
+  h->carrier_flops = carrier_flops_of(nsec, m, n, rows1, nkb1, nkb2, bysrc, bydst, h->lev1, h->lev2);
 
   int rc;
   h->bytes_scratch = (long long)stoff[nsec] * 8 + 2 * h->dim * 8;
@@ -630,6 +564,7 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
   for (int t = 0; t < ntask; ++t) { h->tsrc[t] = tasks[t].src; h->tdst[t] = tasks[t].dst; }
   for (auto& e : h->ev) OZ_CU(cudaEventCreate(&e));
   if (mode == OZ_MODE_NATIVE) h->prepared = true;
+  else if (int rc2 = oz::heff_operator_hist(h, tasks)) return bail(rc2);
   *out = h;
   return OZ_OK;
 }
@@ -695,7 +630,9 @@ int oz_heff_s::prepare() {
         P.mode = oz::OUT_ROWTABLE; P.C = this->dStage; P.ldc = 0;
         P.rowdst = dRowdst + A1row[q]; P.rowslot = dRowslot + A1row[q]; P.rowmax = this->mA2;
         P.alpha = 1.0; P.beta = 0.0;
+        P.s = lev1[q];
         p1.push_back(P);
+        this->p1sec.push_back(q);
       }
       if (!bydst[q].empty()) {
         GemmProblem P{};
@@ -703,7 +640,9 @@ int oz_heff_s::prepare() {
         P.M = m[q]; P.N = n[q]; P.nkb = nkb2[q]; P.SA = S; P.SB = S; P.s = s;
         P.mode = oz::OUT_DENSE; P.C = this->dY + this->psioff[q]; P.ldc = n[q];
         P.alpha = 1.0; P.beta = 0.0;
+        P.s = lev2[q];
         p2.push_back(P);
+        this->p2sec.push_back(q);
       }
     }
     auto make_tiles = [](const std::vector<GemmProblem>& ps) {
@@ -718,6 +657,8 @@ int oz_heff_s::prepare() {
       }
       return tl;
     };
+    this->hp1 = p1;
+    this->hp2 = p2;
     std::vector<GemmTile> t1 = make_tiles(p1), t2 = make_tiles(p2);
     this->nt1 = (int)t1.size();
     this->nt2 = (int)t2.size();
@@ -869,5 +810,41 @@ const double* heff_diag_ptr(const oz_heff* h) { return h->dDiag; }
 extern "C" int oz_heff_diag(const oz_heff* h, double* d_diag, oz_stream_t stream) {
   if (!h || !d_diag) return fail(OZ_EINVAL, "null argument");
   OZ_CU(cudaMemcpyAsync(d_diag, h->dDiag, (size_t)h->dim * 8, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return OZ_OK;
+}
+
+int oz_heff_s::set_levels(const int* s1, const int* s2) {
+  if (mode != OZ_MODE_EAGER) return fail(OZ_EINVAL, "slice levels exist for the emulated path only");
+  for (int q = 0; q < nsec; ++q) {
+    const int a = s1 ? s1[q] : s, b = s2 ? s2[q] : s;
+    if (a < 1 || a > s || b < 1 || b > s)
+      return fail(OZ_EINVAL, "per-sector levels must be in 1..the handle's level (" + std::to_string(s) + ")");
+  }
+  if (int rc = prepare()) return rc;
+  for (int q = 0; q < nsec; ++q) {
+    lev1[q] = s1 ? s1[q] : s;
+    lev2[q] = s2 ? s2[q] : s;
+  }
+  for (size_t i = 0; i < hp1.size(); ++i) hp1[i].s = lev1[p1sec[i]];
+  for (size_t i = 0; i < hp2.size(); ++i) hp2[i].s = lev2[p2sec[i]];
+  // the captured graph reads the problem tables from device memory: rewriting them is enough
+  OZ_CU(cudaDeviceSynchronize());
+  if (!hp1.empty()) OZ_CU(cudaMemcpy(dP1, hp1.data(), hp1.size() * sizeof(GemmProblem), cudaMemcpyHostToDevice));
+  if (!hp2.empty()) OZ_CU(cudaMemcpy(dP2, hp2.data(), hp2.size() * sizeof(GemmProblem), cudaMemcpyHostToDevice));
+  carrier_flops = carrier_flops_of(nsec, m.data(), n.data(), rows1, nkb1, nkb2, bysrc, bydst, lev1, lev2);
+  return OZ_OK;
+}
+
+extern "C" int oz_heff_set_levels(oz_heff* h, const int* s1, const int* s2) {
+  if (!h) return fail(OZ_EINVAL, "handle is null");
+  return h->set_levels(s1, s2);
+}
+
+extern "C" int oz_heff_get_levels(const oz_heff* h, int* s1, int* s2) {
+  if (!h) return fail(OZ_EINVAL, "handle is null");
+  for (int q = 0; q < h->nsec; ++q) {
+    if (s1) s1[q] = h->lev1[q];
+    if (s2) s2[q] = h->lev2[q];
+  }
   return OZ_OK;
 }

@@ -26,4 +26,7 @@ const double* heff_diag_ptr(const oz_heff* h);
 int build_heff_diag(int nsec, const int* m, const int* n, const long long* psioff, int ntask, const oz_task* tasks,
                     double* d_diag);
 
+// Exponent-gap histograms of the operator blocks of a new emulated handle (oz_select.cu).
+int heff_operator_hist(oz_heff* h, const oz_task* tasks);
+
 }  // namespace oz

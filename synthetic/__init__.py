@@ -82,14 +82,14 @@ def _u01(bits: torch.Tensor) -> torch.Tensor:
     return _srl(bits, 11).to(torch.float64) * (2.0 ** -53)
 
 
-def _values(idx: torch.Tensor, key, spread: bool) -> torch.Tensor:
+def _values(idx: torch.Tensor, key, spread: bool, width: int = 20) -> torch.Tensor:
     s = _u01(_lanes(idx, key, 0))
     s = s + _u01(_lanes(idx, key, 1))
     s = s + _u01(_lanes(idx, key, 2))
     s = s + _u01(_lanes(idx, key, 3))
     v = (s - 2.0) * math.sqrt(3.0)
     if spread:
-        j = _srl(_lanes(idx, key, 4), 11) % 20  # uniform on 0..19 up to 2^-48
+        j = _srl(_lanes(idx, key, 4), 11) % width  # uniform on 0..width-1 up to 2^-48
         u = _u01(_lanes(idx, key, 5))
         v = v * torch.ldexp(1.0 + u, -j.to(torch.int32))
     return v
@@ -105,10 +105,12 @@ def normal(seed: int, stream: int, n: int, device="cpu") -> torch.Tensor:
     return _values(torch.arange(n, dtype=torch.int64, device=device), _key(seed, stream), False)
 
 
-def block_values(seed: int, stream: int, rows: int, cols: int, spread: bool, device="cpu") -> torch.Tensor:
-    """A rows x cols float64 block; ``spread`` applies the six-decade exponent spread."""
+def block_values(seed: int, stream: int, rows: int, cols: int, spread: bool, device="cpu",
+                 width: int = 20) -> torch.Tensor:
+    """A rows x cols float64 block; ``spread`` applies the exponent spread 2^-j, j uniform on
+    0..width-1 (width 20: the six-decade spread)."""
     idx = torch.arange(rows * cols, dtype=torch.int64, device=device)
-    return _values(idx, _key(seed, stream), spread).reshape(rows, cols)
+    return _values(idx, _key(seed, stream), spread, width).reshape(rows, cols)
 
 
 # --------------------------------------------------------------------------------------------
@@ -161,6 +163,7 @@ class HeffStructure:
     spread: bool
     seed: int
     partner: np.ndarray = field(default=None)   # task index of the transpose partner
+    widths: np.ndarray = field(default=None)    # per-sector spread widths (None: 20 everywhere)
 
     @property
     def nsec(self) -> int:
@@ -186,7 +189,8 @@ def _loguniform_int(rng, lo, hi, size):
     return np.floor(np.exp(rng.uniform(math.log(lo), math.log(hi + 1), size))).astype(np.int64).clip(lo, hi)
 
 
-def heff_structure(grid=(8, 5), dims=(8, 256), nterms=128, spread=True, seed=1) -> HeffStructure:
+def heff_structure(grid=(8, 5), dims=(8, 256), nterms=128, spread=True, seed=1,
+                   widths: bool = False) -> HeffStructure:
     """Synthetic sector structure.
 
     ``grid`` = (number of particle-number values, number of 2Sz values) of
@@ -195,7 +199,9 @@ def heff_structure(grid=(8, 5), dims=(8, 256), nterms=128, spread=True, seed=1) 
     Hamiltonian terms (Delta=0), then about 20% one-fermion (dN=+-1,
     d2Sz=+-1), 40% pair (dN in {+-2, 0}, d2Sz in {0, +-2}) and 40% density-like
     (Delta=0) terms, all in transpose pairs.  A task exists only where
-    src + Delta is a sector of the grid.
+    src + Delta is a sector of the grid.  ``widths=True`` draws a spread width w_q on 1..20 per
+    sector; the blocks of a task between sectors a and b then use width (w_a + w_b) // 2, so that
+    the exponent spread differs between the stacked products of different sectors.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     A, B = grid
@@ -239,7 +245,8 @@ def heff_structure(grid=(8, 5), dims=(8, 256), nterms=128, spread=True, seed=1) 
     partner = np.empty(len(tasks), dtype=np.int64)
     for i, (k, s, d) in enumerate(tasks):
         partner[i] = pos[(int(k) ^ 1, int(d), int(s))]
-    return HeffStructure(labels, m, n, deltas, np.asarray(coefs), tasks, spread, seed, partner)
+    w = rng.integers(1, 21, size=nsec) if widths else None
+    return HeffStructure(labels, m, n, deltas, np.asarray(coefs), tasks, spread, seed, partner, w)
 
 
 def _task_stream(st: HeffStructure, t: int, side: int) -> int:
@@ -256,8 +263,9 @@ def gen_task_blocks(st: HeffStructure, t: int, value_seed: int = 2, device="cpu"
     odd = k % 2 == 1
     if odd:
         s, d = d, s
-    Lb = block_values(value_seed, _task_stream(st, t, 0), int(st.m[d]), int(st.m[s]), st.spread, device)
-    Rb = block_values(value_seed, _task_stream(st, t, 1), int(st.n[d]), int(st.n[s]), st.spread, device)
+    w = 20 if st.widths is None else int(st.widths[s] + st.widths[d]) // 2
+    Lb = block_values(value_seed, _task_stream(st, t, 0), int(st.m[d]), int(st.m[s]), st.spread, device, w)
+    Rb = block_values(value_seed, _task_stream(st, t, 1), int(st.n[d]), int(st.n[s]), st.spread, device, w)
     if odd:
         Lb, Rb = Lb.T.contiguous(), Rb.T.contiguous()
     return Lb, Rb
@@ -268,6 +276,8 @@ def gen_all_task_blocks(st: HeffStructure, value_seed: int = 2, device="cuda", c
 
     Returns (Lbuf, Rbuf, Loff, Roff): flat float64 buffers and per-task element offsets; task t's
     L block is Lbuf[Loff[t]:Loff[t]+m[dst]*m[src]].view(m[dst], m[src]) (likewise R with n)."""
+    if st.widths is not None:
+        raise ValueError("per-sector spread widths: use gen_task_blocks")
     t = st.tasks
     mdst, msrc = st.m[t[:, 2]].astype(np.int64), st.m[t[:, 1]].astype(np.int64)
     ndst, nsrc = st.n[t[:, 2]].astype(np.int64), st.n[t[:, 1]].astype(np.int64)
@@ -308,13 +318,22 @@ def gen_all_task_blocks(st: HeffStructure, value_seed: int = 2, device="cuda", c
     return out[0], out[2], out[1], out[3]
 
 
-def gen_psi(st: HeffStructure, seed: int = 3, device="cpu") -> torch.Tensor:
-    """psi as one flat float64 vector (blocks q = 0.. concatenated, each row-major)."""
+def gen_psi(st: HeffStructure, seed: int = 3, device="cpu", decades: float = 0.0) -> torch.Tensor:
+    """psi as one flat float64 vector (blocks q = 0.. concatenated, each row-major).
+
+    ``decades`` > 0 scales block q by 2^-round(decades log2(10) u_q), u_q uniform on [0, 1): sector
+    weights spread over that many decades, as the quantum-number sectors of a DMRG wavefunction."""
     off = st.psi_offsets()
     v = normal(seed, 1 << 40, int(off[-1]), device)
     # scale by a power of two so that |psi| is about 1 (exact on every device)
     e = -int(round(0.5 * math.log2(max(1, int(off[-1])))))
-    return torch.ldexp(v, torch.tensor(e, dtype=torch.int32, device=device))
+    v = torch.ldexp(v, torch.tensor(e, dtype=torch.int32, device=device))
+    if decades > 0.0:
+        u = uniform01(seed, (1 << 40) + 1, st.nsec).numpy()
+        for q in range(st.nsec):
+            k = -int(round(decades * math.log2(10.0) * float(u[q])))
+            v[off[q]:off[q + 1]] = torch.ldexp(v[off[q]:off[q + 1]], torch.tensor(k, dtype=torch.int32, device=device))
+    return v
 
 
 # Workload shapes named after what they are (block count, sizes, terms).

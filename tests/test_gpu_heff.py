@@ -103,3 +103,31 @@ def test_heff_symmetric(ctx):
     lhs, rhs = float(x @ hz), float(hx @ z)
     assert abs(lhs - rhs) <= 1e-13 * float(hx.norm() * z.norm())
     h.close()
+
+
+def test_heff_per_sector_levels_bitexact(ctx):
+    """The precision dial per block: random levels per stage-1 (source) and stage-2 (target)
+    product reproduce the oracle's emulation with the same levels bit for bit; the carrier flops
+    follow the levels; restoring the full level restores the default result."""
+    import paper_2510_04795_gb300 as oz
+    st, blocks, psi = _problem((4, 3), (5, 70), 8, True, 7)
+    h = oz.Heff(ctx, st.m, st.n, _tasks(st, blocks), slices=7)
+    y7 = h.apply(psi).clone()
+    f7 = h.info()["carrier_flops"]
+    rng = np.random.default_rng(3)
+    s1 = [int(x) for x in rng.integers(3, 8, size=st.nsec)]
+    s2 = [int(x) for x in rng.integers(3, 8, size=st.nsec)]
+    h.set_levels(s1, s2)
+    assert h.get_levels() == (s1, s2)
+    y = h.apply(psi)
+    ctx.status()
+    Lb = [b[0].cpu().numpy() for b in blocks]
+    Rb = [b[1].cpu().numpy() for b in blocks]
+    ref = heff.heff_apply_emulated(st, Lb, Rb, psi.cpu().numpy(), 7, s1=s1, s2=s2)
+    assert np.array_equal(y.cpu().numpy().view(np.int64), ref.view(np.int64))
+    assert h.info()["carrier_flops"] < f7
+    h.set_levels(None, None)
+    assert torch.equal(h.apply(psi), y7)
+    with pytest.raises(oz.OzError):
+        h.set_levels([8] * st.nsec, None)      # above the handle's level
+    h.close()
