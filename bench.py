@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--no-native", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-validate", action="store_true", help="skip the |dE| check of the two-site sweep")
     return p.parse_args()
 
 
@@ -212,6 +213,42 @@ def workload_config(args, st, cfg):
             "l2": "inputs larger than L2 (operator digit planes are > 100 GB)"}
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """Largest value of x over the ranks of the process group (x itself at world size 1).  The
+    replicas share nothing but this reduction of their timings."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def validation_sweep(ctx, slices: int):
+    """|dE| of the emulated two-site sweep on the 4900-determinant ab initio system (L = N = 8,
+    Sz = 0, D = 64, 4 sweeps): against the explicit-basis oracle at every bond, and against FCI."""
+    import numpy as np
+    import synthetic
+    import paper_2510_04795_gb300 as oz
+    from oracle import dmrg as OD
+    from oracle import fci as OF
+    h1, eri = synthetic.integrals(8, seed=0)
+    t0 = time.perf_counter()
+    e_gpu = oz.dmrg_sweep(ctx, h1, eri, 8, 0, 64, 4, slices=slices)
+    t_gpu = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    e_or = np.array(OD.ExplicitDMRG(h1, eri, 8, 0, 64).sweep(4))
+    t_or = time.perf_counter() - t0
+    e_fci = OF.ground_state(h1, eri, 8, 0)[0]
+    return {"workload": "ab initio L=8 N=8 Sz=0 (FCI dim 4900), D=64, 4 sweeps, emulated S=%d" % slices,
+            "dE_vs_oracle_max_Eh": float(np.max(np.abs(e_gpu - e_or))), "E_final_Eh": float(e_gpu[-1]),
+            "E_fci_Eh": float(e_fci), "E_final_minus_fci_Eh": float(e_gpu[-1] - e_fci),
+            "middle_bond_minus_fci_Eh": float(e_gpu[-2 * 7 + 3] - e_fci),
+            "sweep_s_gpu": t_gpu, "sweep_s_oracle_cpu": t_or}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -291,11 +328,7 @@ def main():
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
     ctx.status()
     stage = [v / args.steps for v in stage]
 
@@ -313,11 +346,7 @@ def main():
     for _ in range(args.steps):
         oz.heff_apply_host(h, psi_h, y_h)
         torch.cuda.current_stream().synchronize()
-    ms_e2e = (time.perf_counter() - t0) * 1e3 / args.steps
-    if world > 1:
-        t = torch.tensor([ms_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, world)
     ok_e2e = bool(torch.equal(y_h, y.cpu()))
 
     pk, pk_src = peaks()
@@ -343,6 +372,11 @@ def main():
                "sample": f"{sub.ntask} of {st.ntask} tasks (all tasks into the first target sectors), "
                          f"{fl:.3e} FP64 flop, {dt:.1f} s, numpy per-block products on the host BLAS"}
 
+    validation = None
+    if rank == 0 and not args.no_validate:
+        h.close()
+        validation = validation_sweep(ctx, S)
+
     value = world * F / (ms * 1e-3) / 1e12
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -360,6 +394,7 @@ def main():
         "carrier_flop_per_step_padded": info["carrier_flops"],
         "device_bytes": {"operators": info["bytes_ops"], "scratch": info["bytes_scratch"]},
         "clocks": clk,
+        "validation": validation,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)

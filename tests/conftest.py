@@ -13,6 +13,13 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: takes more than a few seconds on the CPU")
 
 
+def pytest_sessionstart(session):
+    # the library is built in-tree (no-op when its sources are unchanged); nvcc cross-compiles
+    # without a GPU, so the host-only tests (MPO, exports) also run on a machine without one
+    from paper_2510_04795_gb300 import build
+    build.build()
+
+
 def pytest_collection_modifyitems(config, items):
     try:
         import torch
