@@ -322,16 +322,17 @@ namespace {
 long long carrier_flops_of(int nsec, const int* m, const int* n, const std::vector<int>& rows1,
                            const std::vector<int>& nkb1, const std::vector<int>& nkb2,
                            const std::vector<std::vector<int>>& bysrc, const std::vector<std::vector<int>>& bydst,
-                           const std::vector<int>& lev1, const std::vector<int>& lev2) {
+                           const std::vector<int>& lev1, const std::vector<int>& lev2, const std::vector<char>& swap2) {
   long long f = 0;
   for (int q = 0; q < nsec; ++q) {
     const long long P1 = (long long)lev1[q] * (lev1[q] + 1) / 2, P2 = (long long)lev2[q] * (lev2[q] + 1) / 2;
     if (!bysrc[q].empty())
       f += P1 * 2 * (cdiv(rows1[q], oz::TILE_M) * oz::TILE_M) * (cdiv(n[q], oz::BN) * oz::BN) *
            ((long long)nkb1[q] * oz::KB);
-    if (!bydst[q].empty())
-      f += P2 * 2 * (cdiv(m[q], oz::TILE_M) * oz::TILE_M) * (cdiv(n[q], oz::BN) * oz::BN) *
-           ((long long)nkb2[q] * oz::KB);
+    if (!bydst[q].empty()) {
+      const long long r2 = swap2[q] ? n[q] : m[q], c2 = swap2[q] ? m[q] : n[q];
+      f += P2 * 2 * (cdiv(r2, oz::TILE_M) * oz::TILE_M) * (cdiv(c2, oz::BN) * oz::BN) * ((long long)nkb2[q] * oz::KB);
+    }
   }
   return f;
 }
@@ -416,19 +417,26 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
   const long long A1tile = (long long)oz::TILE_M * oz::KB, Btile = (long long)oz::BN * oz::KB;
   std::vector<long long> A1off(nsec + 1, 0), B1off(nsec + 1, 0), A2off(nsec + 1, 0), B2off(nsec + 1, 0);
   std::vector<long long> A1row(nsec + 1, 0), B1row(nsec + 1, 0), A2row(nsec + 1, 0), B2row(nsec + 1, 0);
+  h->swap2.assign(nsec, 0);
+  for (int q = 0; q < nsec; ++q)
+    h->swap2[q] = cdiv(n[q], oz::TILE_M) * oz::TILE_M * cdiv(m[q], oz::BN) * oz::BN <
+                  cdiv(m[q], oz::TILE_M) * oz::TILE_M * cdiv(n[q], oz::BN) * oz::BN;
   for (int q = 0; q < nsec; ++q) {
     long long nrbA1 = cdiv(rows1[q], oz::TILE_M), nrbB1 = cdiv(n[q], oz::BN);
-    long long nrbA2 = cdiv(m[q], oz::TILE_M), nrbB2 = cdiv(n[q], oz::BN);
+    // stage 2: T (m[q] rows) and the (cR) stack (n[q] rows) take the 128- and 64-row sides of the
+    // tile, or the other way round when the handle computes this sector transposed
+    const long long trA2 = h->swap2[q] ? oz::BN : oz::TILE_M, trB2 = h->swap2[q] ? oz::TILE_M : oz::BN;
+    long long nrbA2 = cdiv(m[q], trA2), nrbB2 = cdiv(n[q], trB2);
     A1off[q + 1] = A1off[q] + nrbA1 * nkb1[q] * S * A1tile;
     B1off[q + 1] = B1off[q] + nrbB1 * nkb1[q] * S * Btile;
-    A2off[q + 1] = A2off[q] + nrbA2 * nkb2[q] * S * A1tile;
-    B2off[q + 1] = B2off[q] + nrbB2 * nkb2[q] * S * Btile;
+    A2off[q + 1] = A2off[q] + nrbA2 * nkb2[q] * S * trA2 * oz::KB;
+    B2off[q + 1] = B2off[q] + nrbB2 * nkb2[q] * S * trB2 * oz::KB;
     A1row[q + 1] = A1row[q] + nrbA1 * oz::TILE_M;
     B1row[q + 1] = B1row[q] + nrbB1 * oz::BN;
-    A2row[q + 1] = A2row[q] + nrbA2 * oz::TILE_M;
-    B2row[q + 1] = B2row[q] + nrbB2 * oz::BN;
+    A2row[q + 1] = A2row[q] + nrbA2 * trA2;
+    B2row[q + 1] = B2row[q] + nrbB2 * trB2;
   }
-  h->carrier_flops = carrier_flops_of(nsec, m, n, rows1, nkb1, nkb2, bysrc, bydst, h->lev1, h->lev2);
+  h->carrier_flops = carrier_flops_of(nsec, m, n, rows1, nkb1, nkb2, bysrc, bydst, h->lev1, h->lev2, h->swap2);
 
   int rc;
   h->bytes_scratch = (long long)stoff[nsec] * 8 + 2 * h->dim * 8;
@@ -525,7 +533,7 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
         SliceSeg g{};
         g.src = tk.d_R; g.ld = n[tk.src]; g.rows = n[q]; g.cols = n[tk.src]; g.prows = g.rows; g.pcols = g.cols;
         g.r0 = 0; g.k0 = (int)offk[t]; g.trans = 0; g.S = S; g.scale = tk.coef;
-        g.dst = h->dB2 + B2off[q]; g.TR = oz::BN; g.nkb = nkb2[q];
+        g.dst = h->dB2 + B2off[q]; g.TR = h->swap2[q] ? oz::TILE_M : oz::BN; g.nkb = nkb2[q];
         g.rowmax = mB2 + B2row[q]; g.rowexp = eB2 + B2row[q];
         g.unit0 = ud; g.unit0m = um;
         ud += oz::digit_units(g.prows, g.pcols);
@@ -636,9 +644,15 @@ int oz_heff_s::prepare() {
       }
       if (!bydst[q].empty()) {
         GemmProblem P{};
-        P.A = this->dA2 + A2off[q]; P.B = this->dB2 + B2off[q]; P.ea = this->eA2 + A2row[q]; P.eb = eB2 + B2row[q];
-        P.M = m[q]; P.N = n[q]; P.nkb = nkb2[q]; P.SA = S; P.SB = S; P.s = s;
-        P.mode = oz::OUT_DENSE; P.C = this->dY + this->psioff[q]; P.ldc = n[q];
+        if (!swap2[q]) {
+          P.A = this->dA2 + A2off[q]; P.B = this->dB2 + B2off[q]; P.ea = this->eA2 + A2row[q]; P.eb = eB2 + B2row[q];
+          P.M = m[q]; P.N = n[q]; P.mode = oz::OUT_DENSE;
+        } else {  // Y^T = (cR stack) T^T: identical elements (the rounding of each is unchanged)
+          P.A = this->dB2 + B2off[q]; P.B = this->dA2 + A2off[q]; P.ea = eB2 + B2row[q]; P.eb = this->eA2 + A2row[q];
+          P.M = n[q]; P.N = m[q]; P.mode = oz::OUT_DENSE_T;
+        }
+        P.nkb = nkb2[q]; P.SA = S; P.SB = S; P.s = s;
+        P.C = this->dY + this->psioff[q]; P.ldc = n[q];
         P.alpha = 1.0; P.beta = 0.0;
         P.s = lev2[q];
         p2.push_back(P);
@@ -691,7 +705,7 @@ int oz_heff_s::prepare() {
       SliceSeg g{};
       g.src = this->dStage + stoff[q]; g.ld = ld2[q]; g.rows = m[q]; g.cols = ld2[q]; g.prows = g.rows;
       g.pcols = g.cols; g.r0 = 0; g.k0 = 0; g.trans = 0; g.S = S; g.scale = 1.0;
-      g.dst = this->dA2 + A2off[q]; g.TR = oz::TILE_M; g.nkb = nkb2[q];
+      g.dst = this->dA2 + A2off[q]; g.TR = swap2[q] ? oz::BN : oz::TILE_M; g.nkb = nkb2[q];
       g.rowmax = this->mA2 + A2row[q]; g.rowexp = this->eA2 + A2row[q];
       g.unit0 = ad; g.unit0m = 0;
       ad += oz::digit_units(g.prows, g.pcols);
@@ -831,7 +845,7 @@ int oz_heff_s::set_levels(const int* s1, const int* s2) {
   OZ_CU(cudaDeviceSynchronize());
   if (!hp1.empty()) OZ_CU(cudaMemcpy(dP1, hp1.data(), hp1.size() * sizeof(GemmProblem), cudaMemcpyHostToDevice));
   if (!hp2.empty()) OZ_CU(cudaMemcpy(dP2, hp2.data(), hp2.size() * sizeof(GemmProblem), cudaMemcpyHostToDevice));
-  carrier_flops = carrier_flops_of(nsec, m.data(), n.data(), rows1, nkb1, nkb2, bysrc, bydst, lev1, lev2);
+  carrier_flops = carrier_flops_of(nsec, m.data(), n.data(), rows1, nkb1, nkb2, bysrc, bydst, lev1, lev2, swap2);
   return OZ_OK;
 }
 

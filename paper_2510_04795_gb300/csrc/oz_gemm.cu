@@ -347,7 +347,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int ebl = (lane < CW && col0 + lane < N) ? __ldg(P->eb + col0 + lane) : 0;
       const int ea_raw = rowok ? __ldg(P->ea + row) : 0;
       double* crow = nullptr;
-      if (rowok) crow = (mode == OUT_DENSE ? P->C + (long long)row * P->ldc : P->C + __ldg(P->rowdst + row)) + col0;
+      const bool tmode = mode == OUT_DENSE_T;
+      if (rowok) {
+        if (mode == OUT_DENSE) crow = P->C + (long long)row * P->ldc + col0;
+        else if (tmode) crow = P->C + (long long)col0 * P->ldc + row;  // element jj at crow[jj * ldc]
+        else crow = P->C + __ldg(P->rowdst + row) + col0;
+      }
+      const long long cstr = tmode ? P->ldc : 1;
       // exact running sum Z = zhi * 2^32 + zlo; drains with shift < 32 go to zlo, the others to zhi
       // (each part stays below 2^62 in magnitude for levels <= 8 and fewer than 2^13 groups per diagonal)
       long long zlo[CW], zhi[CW];
@@ -388,7 +394,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int ncol = min(CW, N - col0);
       const int ea = ea_raw - 8 * S - 6;
       const double alpha = P->alpha, beta = P->beta;
-      const bool plain = (mode != OUT_DENSE) || ((alpha == 1.0) && (beta == 0.0));
+      const bool plain = (mode == OUT_ROWTABLE) || ((alpha == 1.0) && (beta == 0.0));
       unsigned long long mx = 0;
 #pragma unroll
       for (int c4 = 0; c4 < CW / ZC; ++c4) {
@@ -406,17 +412,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               v = z96_to_double(z.x, z.y, ea + ebj);
               if (!plain) {
                 v = __dmul_rn(alpha, v);
-                if (beta != 0.0) v = __dadd_rn(v, __dmul_rn(beta, crow[jj]));
+                if (beta != 0.0) v = __dadd_rn(v, __dmul_rn(beta, crow[jj * cstr]));
               }
               const unsigned long long bb = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
               mx = bb > mx ? bb : mx;
+              // transposed output: the warp's lanes are consecutive rows, i.e. consecutive addresses
+              if (tmode) crow[jj * cstr] = v;
             }
             reinterpret_cast<double*>(zs + lane * ZS_LD + j)[0] = v;
           }
           __syncwarp();
           // coalesced stores: each pass writes (32 / ZC) rows x ZC consecutive doubles
 #pragma unroll 1
-          for (int p = 0; p < ZC; ++p) {
+          for (int p = 0; p < ZC && !tmode; ++p) {
             const int r = p * (32 / ZC) + lane / ZC, cc = lane % ZC;
             double* base =
                 reinterpret_cast<double*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(crow), r));
@@ -425,7 +433,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           __syncwarp();
         }
       }
-      if (mode != OUT_DENSE && rowok && mx && P->rowmax) atomicMax(P->rowmax + __ldg(P->rowslot + row), mx);
+      if (mode == OUT_ROWTABLE && rowok && mx && P->rowmax) atomicMax(P->rowmax + __ldg(P->rowslot + row), mx);
     }
   }
 

@@ -9,7 +9,9 @@ constexpr int NBUF = 512 / BN;      // TMEM accumulator buffers of BN columns
 
 constexpr int MAX_LEVEL = 8;        // slice levels supported by the BN = 64 kernel (one buffer per diagonal)
 
-enum : int { OUT_DENSE = 0, OUT_ROWTABLE = 1 };
+// output modes: dense C[row * ldc + col]; row table (C + rowdst[row] + col, with per-row |max|);
+// dense transposed C[col * ldc + row]
+enum : int { OUT_DENSE = 0, OUT_ROWTABLE = 1, OUT_DENSE_T = 2 };
 
 // One emulated product C = alpha * (A B) + beta * C at slice level s.
 // A: M x K as tiled digit planes (TILE_M-row tiles), B^T: N x K as tiled planes (BN-row tiles).
@@ -21,7 +23,7 @@ struct GemmProblem {
   int M, N, nkb;               // sizes, k-blocks of KB
   int SA, SB;                  // planes stored per k-block in A / B^T
   int s;                       // slice level (1..MAX_LEVEL)
-  int mode;                    // OUT_DENSE or OUT_ROWTABLE
+  int mode;                    // OUT_DENSE, OUT_ROWTABLE or OUT_DENSE_T
   double* C;                   // dense: C + row * ldc + col;  rowtable: C + rowdst[row] + col
   long long ldc;
   const long long* rowdst;

@@ -87,6 +87,9 @@ struct oz_heff_s {
   std::vector<oz::GemmProblem> hp1, hp2;
   std::vector<int> p1sec, p2sec;
   std::vector<int> lev1, lev2;  // per source sector (stage 1), per target sector (stage 2)
+  // stage-2 orientation per target sector: 1 = computed as Y^T = (cR stack) T^T, so that the
+  // smaller of m[q], n[q] takes the 64-row side of the tile (less padding)
+  std::vector<char> swap2;
   // exponent-gap histograms of the operators (9 bins per sector): stage-1 A, stage-2 B
   std::vector<unsigned long long> histA1, histB2;
   int set_levels(const int* s1, const int* s2);

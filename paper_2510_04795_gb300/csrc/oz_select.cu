@@ -407,9 +407,11 @@ extern "C" int oz_heff_select_levels(oz_heff* h, const double* d_psi, int select
       for (int q = 0; q < nsec; ++q) {
         if (stage == 0 ? h->bysrc[q].empty() : h->bydst[q].empty()) continue;
         prob.push_back(q);
-        const double M = stage == 0 ? h->rows1[q] : h->m[q];
+        const bool sw = stage == 1 && h->swap2[q];
+        const double M = stage == 0 ? h->rows1[q] : (sw ? h->n[q] : h->m[q]);
+        const double Nn = sw ? h->m[q] : h->n[q];
         const double K = (stage == 0 ? h->nkb1[q] : h->nkb2[q]) * (double)oz::KB;
-        size[q] = 2.0 * std::ceil(M / oz::TILE_M) * oz::TILE_M * std::ceil((double)h->n[q] / oz::BN) * oz::BN * K;
+        size[q] = 2.0 * std::ceil(M / oz::TILE_M) * oz::TILE_M * std::ceil(Nn / oz::BN) * oz::BN * K;
       }
       auto err2 = [&](int q, int l) {
         if (on[q] <= 0.0) return 0.0;
