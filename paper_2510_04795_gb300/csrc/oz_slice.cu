@@ -95,11 +95,29 @@ __global__ void __launch_bounds__(256) digits_kernel(const SliceSeg* __restrict_
   const bool rowok = i < g.rows;
   int e = rowok ? exponent_from_maxbits(g.rowmax[R]) : 0;
   if (c == 0) g.rowexp[R] = e;
+  // the 8 values: one 64-byte run of the row, read as four 16-byte loads where it is aligned
+  double vals[8];
+  const int j0 = c * 8;
+  const double* rp = g.src + (long long)i * g.ld + j0;
+  if (rowok && !g.trans && j0 + 8 <= g.cols && ((reinterpret_cast<uintptr_t>(rp) & 15) == 0)) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const double2 w = __ldg(reinterpret_cast<const double2*>(rp) + q);
+      vals[2 * q] = w.x;
+      vals[2 * q + 1] = w.y;
+    }
+    if (g.scale != 1.0) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) vals[q] = __dmul_rn(vals[q], g.scale);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) vals[q] = (rowok && j0 + q < g.cols) ? load_src(g, i, j0 + q) : 0.0;
+  }
   int d[S][8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    int j = c * 8 + q;
-    double v = (rowok && j < g.cols) ? load_src(g, i, j) : 0.0;
+    const double v = vals[q];
     if constexpr (S <= 8) {
       long long X = fixed_point64(v, e, S);
 #pragma unroll
