@@ -283,12 +283,12 @@ int oz_heff_s::enqueue(cudaStream_t st, bool capturing) {
     OZ_CU(oz::launch_rowmax(dSegPsi, nullptr, nsegPsi, uPsiM, ctx->d_flags, st));
     OZ_CU(oz::launch_digits(dSegPsi, nullptr, nsegPsi, uPsiD, S, st));
     OZ_CU(cudaEventRecordWithFlags(ev[1], st, evf));
-    OZ_CU(oz::launch_gemm(dP1, dT1, nt1, ctx->nsm, nullptr, s, ctx->d_flags + 1, st));
+    OZ_CU(oz::launch_gemm(dP1, dT1, nt1, ctx->nsm, nullptr, s, ctx->d_flags + 1, st, dF1));
     OZ_CU(cudaEventRecordWithFlags(ev[2], st, evf));
     OZ_CU(oz::launch_digits(dSegA2, nullptr, nsegA2, uA2D, S, st));
     if (zero_y) OZ_CU(cudaMemsetAsync(dY, 0, (size_t)dim * 8, st));
     OZ_CU(cudaEventRecordWithFlags(ev[3], st, evf));
-    OZ_CU(oz::launch_gemm(dP2, dT2, nt2, ctx->nsm, nullptr, s, ctx->d_flags + 1, st));
+    OZ_CU(oz::launch_gemm(dP2, dT2, nt2, ctx->nsm, nullptr, s, ctx->d_flags + 1, st, dF2));
     OZ_CU(cudaEventRecordWithFlags(ev[4], st, evf));
     return OZ_OK;
   }
@@ -676,14 +676,17 @@ int oz_heff_s::prepare() {
     std::vector<GemmTile> t1 = make_tiles(p1), t2 = make_tiles(p2);
     this->nt1 = (int)t1.size();
     this->nt2 = (int)t2.size();
+    this->ht1 = t1;
+    this->ht2 = t2;
+    if ((rc = this->alloc(&this->dF1, (size_t)(c->nsm + 1) * 4))) return rc;
+    if ((rc = this->alloc(&this->dF2, (size_t)(c->nsm + 1) * 4))) return rc;
     if ((rc = this->alloc(&this->dP1, std::max<size_t>(1, p1.size()) * sizeof(GemmProblem)))) return rc;
     if ((rc = this->alloc(&this->dP2, std::max<size_t>(1, p2.size()) * sizeof(GemmProblem)))) return rc;
     if ((rc = this->alloc(&this->dT1, std::max<size_t>(1, t1.size()) * sizeof(GemmTile)))) return rc;
     if ((rc = this->alloc(&this->dT2, std::max<size_t>(1, t2.size()) * sizeof(GemmTile)))) return rc;
     if (!p1.empty()) OZ_CU(cudaMemcpy(this->dP1, p1.data(), p1.size() * sizeof(GemmProblem), cudaMemcpyHostToDevice));
     if (!p2.empty()) OZ_CU(cudaMemcpy(this->dP2, p2.data(), p2.size() * sizeof(GemmProblem), cudaMemcpyHostToDevice));
-    if (!t1.empty()) OZ_CU(cudaMemcpy(this->dT1, t1.data(), t1.size() * sizeof(GemmTile), cudaMemcpyHostToDevice));
-    if (!t2.empty()) OZ_CU(cudaMemcpy(this->dT2, t2.data(), t2.size() * sizeof(GemmTile), cudaMemcpyHostToDevice));
+    if ((rc = this->balance())) return rc;
 
     // ---- per-product slicing segments: psi (B of stage 1) and the concatenated T (A of stage 2)
     std::vector<SliceSeg> sp, sa;
@@ -845,6 +848,7 @@ int oz_heff_s::set_levels(const int* s1, const int* s2) {
   OZ_CU(cudaDeviceSynchronize());
   if (!hp1.empty()) OZ_CU(cudaMemcpy(dP1, hp1.data(), hp1.size() * sizeof(GemmProblem), cudaMemcpyHostToDevice));
   if (!hp2.empty()) OZ_CU(cudaMemcpy(dP2, hp2.data(), hp2.size() * sizeof(GemmProblem), cudaMemcpyHostToDevice));
+  if (int rc = balance()) return rc;
   carrier_flops = carrier_flops_of(nsec, m.data(), n.data(), rows1, nkb1, nkb2, bysrc, bydst, lev1, lev2, swap2);
   return OZ_OK;
 }
@@ -860,5 +864,18 @@ extern "C" int oz_heff_get_levels(const oz_heff* h, int* s1, int* s2) {
     if (s1) s1[q] = h->lev1[q];
     if (s2) s2[q] = h->lev2[q];
   }
+  return OZ_OK;
+}
+
+int oz_heff_s::balance() {
+  // tiles of each stage onto the persistent CTAs by cost at the current levels (the problem tables
+  // on the device already hold those levels); same sizes, so the captured graph stays valid
+  std::vector<int> f1, f2;
+  oz::balance_tiles(hp1, ht1, ctx->nsm, f1);
+  oz::balance_tiles(hp2, ht2, ctx->nsm, f2);
+  if (!ht1.empty()) OZ_CU(cudaMemcpy(dT1, ht1.data(), ht1.size() * sizeof(GemmTile), cudaMemcpyHostToDevice));
+  if (!ht2.empty()) OZ_CU(cudaMemcpy(dT2, ht2.data(), ht2.size() * sizeof(GemmTile), cudaMemcpyHostToDevice));
+  OZ_CU(cudaMemcpy(dF1, f1.data(), f1.size() * 4, cudaMemcpyHostToDevice));
+  OZ_CU(cudaMemcpy(dF2, f2.data(), f2.size() * 4, cudaMemcpyHostToDevice));
   return OZ_OK;
 }

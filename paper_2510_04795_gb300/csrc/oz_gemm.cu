@@ -26,6 +26,10 @@
 // Every wait is bounded; a timeout sets *err and all roles leave their loops.
 #include "oz_gemm.cuh"
 
+#include <algorithm>
+#include <utility>
+#include <vector>
+
 namespace oz {
 
 constexpr int A_TILE_BYTES = TILE_M * KB * 2;             // 4 KB per plane
@@ -235,6 +239,7 @@ __device__ __forceinline__ void tile_of(const GemmTile* tiles, const GemmProblem
 
 __global__ void __launch_bounds__(NTHREADS, 1)
     gemm_kernel(const GemmProblem* __restrict__ probs, const GemmTile* __restrict__ tiles, int ntiles,
+                const int* __restrict__ first,
                 const __grid_constant__ GemmProblem single, int smax, int nstage, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -263,13 +268,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = sh.tmem;
+  // this CTA's tiles: the range [first[b], first[b+1]) of a host-balanced list, or every
+  // gridDim.x-th tile; all three roles walk the same sequence
+  const int it0 = first ? first[blockIdx.x] : (int)blockIdx.x;
+  const int it1 = first ? first[blockIdx.x + 1] : ntiles;
+  const int istep = first ? 1 : (int)gridDim.x;
 
   if (warp == 0) {
     // ------------------------------------------------------------------ producer
     if (lane == 0) {
       Ring rg{0, 0, nstage};
       long long fills = 0;
-      for (int idx = blockIdx.x; idx < ntiles && !*abort; idx += gridDim.x) {
+      for (int idx = it0; idx < it1 && !*abort; idx += istep) {
         const GemmProblem* P;
         int mb, nb;
         tile_of(tiles, probs, single, idx, P, mb, nb);
@@ -306,7 +316,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ------------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       MmaCtl c{Ring{0, 0, nstage}, BufRing{0u, 0, 0}, 0u};
-      for (int idx = blockIdx.x; idx < ntiles && !*abort; idx += gridDim.x) {
+      for (int idx = it0; idx < it1 && !*abort; idx += istep) {
         const GemmProblem* P;
         int mb, nb;
         tile_of(tiles, probs, single, idx, P, mb, nb);
@@ -335,7 +345,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint32_t accf_par = 0;
     BufRing er{0u, 0, 0};
     longlong2* zs = zstage + (warp - 2) * 32 * ZS_LD;
-    for (int idx = blockIdx.x; idx < ntiles && !*abort; idx += gridDim.x) {
+    for (int idx = it0; idx < it1 && !*abort; idx += istep) {
       const GemmProblem* P;
       int mb, nb;
       tile_of(tiles, probs, single, idx, P, mb, nb);
@@ -446,8 +456,45 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (threadIdx.x == 0 && sh.abort) atomicOr(err, 2);
 }
 
+void balance_tiles(const std::vector<GemmProblem>& probs, std::vector<GemmTile>& tiles, int grid,
+                   std::vector<int>& first) {
+  // cost in MMA units: k-blocks x slice pairs, plus about 130 MMAs' worth of epilogue per tile
+  auto cost = [&](const GemmTile& t) {
+    const GemmProblem& P = probs[t.prob];
+    return (long long)P.nkb * (P.s * (P.s + 1) / 2) + 130;
+  };
+  std::vector<int> ord(tiles.size());
+  for (size_t i = 0; i < tiles.size(); ++i) ord[i] = (int)i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cost(tiles[a]) > cost(tiles[b]); });
+  // longest first onto the least loaded CTA (ties: lowest index)
+  std::vector<long long> load(grid, 0);
+  std::vector<std::vector<int>> own(grid);
+  std::vector<std::pair<long long, int>> heap;
+  for (int b = 0; b < grid; ++b) heap.push_back({0, b});
+  auto cmp = [](const std::pair<long long, int>& x, const std::pair<long long, int>& y) {
+    return x.first != y.first ? x.first > y.first : x.second > y.second;
+  };
+  std::make_heap(heap.begin(), heap.end(), cmp);
+  for (int i : ord) {
+    std::pop_heap(heap.begin(), heap.end(), cmp);
+    auto& top = heap.back();
+    own[top.second].push_back(i);
+    top.first += cost(tiles[i]);
+    std::push_heap(heap.begin(), heap.end(), cmp);
+  }
+  std::vector<GemmTile> out;
+  out.reserve(tiles.size());
+  first.assign(grid + 1, 0);
+  for (int b = 0; b < grid; ++b) {
+    first[b] = (int)out.size();
+    for (int i : own[b]) out.push_back(tiles[i]);
+  }
+  first[grid] = (int)out.size();
+  tiles.swap(out);
+}
+
 cudaError_t launch_gemm(const GemmProblem* d_probs, const GemmTile* d_tiles, int ntiles, int grid,
-                        const GemmProblem* single, int smax, int* d_err, cudaStream_t st) {
+                        const GemmProblem* single, int smax, int* d_err, cudaStream_t st, const int* d_first) {
   if (ntiles <= 0) return cudaSuccess;
   static bool attr = false;
   if (!attr) {
@@ -462,8 +509,9 @@ cudaError_t launch_gemm(const GemmProblem* d_probs, const GemmTile* d_tiles, int
   }
   if (smax < 1 || smax > MAX_LEVEL) return cudaErrorInvalidValue;
   const int nstage = gemm_stages(smax);
-  gemm_kernel<<<grid < ntiles ? grid : ntiles, NTHREADS, gemm_smem_bytes(smax), st>>>(d_probs, d_tiles, ntiles, one,
-                                                                                      smax, nstage, d_err);
+  const int g = d_first ? grid : (grid < ntiles ? grid : ntiles);
+  gemm_kernel<<<g, NTHREADS, gemm_smem_bytes(smax), st>>>(d_probs, d_tiles, ntiles, d_first, one, smax, nstage,
+                                                          d_err);
   return cudaGetLastError();
 }
 

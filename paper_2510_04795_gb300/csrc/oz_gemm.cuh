@@ -1,5 +1,6 @@
 // Grouped persistent Ozaki GEMM on tcgen05 (declarations).
 #pragma once
+#include <vector>
 #include "oz_common.cuh"
 
 namespace oz {
@@ -38,8 +39,16 @@ struct GemmTile {
 
 size_t gemm_smem_bytes(int smax);
 // tiles == nullptr: a single problem (*single) with implicit tiles i -> (i / nnb, i % nnb);
-// otherwise smax is the largest slice level among the launch's problems (sizes the pipeline stages)
+// otherwise smax is the largest slice level among the launch's problems (sizes the pipeline stages).
+// d_first (grid + 1 entries, optional): CTA b processes tiles [d_first[b], d_first[b+1]) in order;
+// without it CTA b takes tiles b, b + grid, ...
 cudaError_t launch_gemm(const GemmProblem* d_probs, const GemmTile* d_tiles, int ntiles, int grid,
-                        const GemmProblem* single, int smax, int* d_err, cudaStream_t st);
+                        const GemmProblem* single, int smax, int* d_err, cudaStream_t st,
+                        const int* d_first = nullptr);
+// Balanced assignment of a tile list to `grid` CTAs (longest processing time first, cost of a
+// tile = k-blocks x slice pairs + a fixed epilogue share): reorders `tiles` so that CTA b owns
+// the range [first[b], first[b+1]).
+void balance_tiles(const std::vector<GemmProblem>& probs, std::vector<GemmTile>& tiles, int grid,
+                   std::vector<int>& first);
 
 }  // namespace oz
