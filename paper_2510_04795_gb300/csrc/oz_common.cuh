@@ -265,16 +265,12 @@ OZ_DEVICE_INLINE double split_to_double(long long zhi, long long zlo, int E) {
   return __longlong_as_double((long long)(sign | ((unsigned long long)(e2 + 1023) << 52) | (m & ((1ull << 52) - 1))));
 }
 
-// Same rounding as split_to_double with 32-bit word arithmetic only: Z = zhi * 2^32 + zlo is
-// formed as a 96-bit two's-complement number w2:w1:w0 (|zhi|, |zlo| < 2^62 so |Z| < 2^95),
-// normalised by whole words and one funnel shift, rounded to 53 bits (ties to even) with a sticky
-// bit, and assembled directly; results outside the normal range take the general path.
-OZ_DEVICE_INLINE double z96_to_double(long long zhi, long long zlo, int E) {
-  const uint32_t l0 = (uint32_t)zlo, l1 = (uint32_t)((unsigned long long)zlo >> 32);
-  const uint32_t h0 = (uint32_t)zhi, h1 = (uint32_t)((unsigned long long)zhi >> 32);
-  const uint32_t sx = (uint32_t)((int32_t)l1 >> 31);
-  uint32_t w0 = l0, w1, w2;
-  asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, %5;" : "=r"(w1), "=r"(w2) : "r"(l1), "r"(h0), "r"(h1), "r"(sx));
+// RN_even(Z * 2^E) for the 96-bit two's-complement integer Z = w2:w1:w0 (|Z| < 2^95), with the
+// rounding of split_to_double in 32-bit word arithmetic only: normalised by whole words and one
+// funnel shift, rounded to 53 bits (ties to even) with a sticky bit, and assembled directly;
+// results outside the normal range take the general path.
+OZ_DEVICE_INLINE double w96_to_double(uint32_t w0, uint32_t w1, uint32_t w2, int E) {
+  const uint32_t v0 = w0, v1 = w1, v2 = w2;
   const uint32_t sign = w2 & 0x80000000u;
   if (sign) asm("sub.cc.u32 %0, 0, %0;\n\tsubc.cc.u32 %1, 0, %1;\n\tsubc.u32 %2, 0, %2;" : "+r"(w0), "+r"(w1), "+r"(w2));
   if ((w0 | w1 | w2) == 0u) return 0.0;
@@ -308,8 +304,36 @@ OZ_DEVICE_INLINE double z96_to_double(long long zhi, long long zlo, int E) {
       e2 += 1;
     }
   }
-  if (e2 < -1022 || e2 > 1023) return int128_to_double(((__int128)zhi << 32) + (__int128)zlo, E);
+  if (e2 < -1022 || e2 > 1023) {
+    const __int128 Z = (__int128)(((unsigned __int128)(int32_t)v2 << 64) | ((unsigned __int128)v1 << 32) | v0);
+    return int128_to_double(Z, E);
+  }
   return __hiloint2double((int)(sign | ((uint32_t)(e2 + 1023) << 20) | (mh & 0xFFFFFu)), (int)ml);
+}
+
+// The same for Z = zhi * 2^32 + zlo (|zhi|, |zlo| < 2^62, so |Z| < 2^95).
+OZ_DEVICE_INLINE double z96_to_double(long long zhi, long long zlo, int E) {
+  const uint32_t l0 = (uint32_t)zlo, l1 = (uint32_t)((unsigned long long)zlo >> 32);
+  const uint32_t h0 = (uint32_t)zhi, h1 = (uint32_t)((unsigned long long)zhi >> 32);
+  const uint32_t sx = (uint32_t)((int32_t)l1 >> 31);
+  uint32_t w1, w2;
+  asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, %5;" : "=r"(w1), "=r"(w2) : "r"(l1), "r"(h0), "r"(h1), "r"(sx));
+  return w96_to_double(l0, w1, w2, E);
+}
+
+// Z += x * 2^sh for an int32 x and 0 <= sh < 64, on the 96-bit two's-complement Z = w2:w1:w0.
+OZ_DEVICE_INLINE void w96_add_shifted(uint32_t& w0, uint32_t& w1, uint32_t& w2, int x, int sh) {
+  const int b = sh & 31;
+  const uint32_t lo = (uint32_t)x << b;
+  const uint32_t hi = b ? (uint32_t)(x >> (32 - b)) : (uint32_t)(x >> 31);
+  const uint32_t sg = (uint32_t)(x >> 31);
+  if (sh < 32) {
+    asm("add.cc.u32 %0, %0, %3;\n\taddc.cc.u32 %1, %1, %4;\n\taddc.u32 %2, %2, %5;"
+        : "+r"(w0), "+r"(w1), "+r"(w2)
+        : "r"(lo), "r"(hi), "r"(sg));
+  } else {
+    asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, %3;" : "+r"(w1), "+r"(w2) : "r"(lo), "r"(hi));
+  }
 }
 
 }  // namespace oz

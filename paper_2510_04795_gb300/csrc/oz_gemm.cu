@@ -198,10 +198,11 @@ __device__ void mma_tile(Shared& sh, MmaCtl& c, uint32_t tmem, uint32_t stage0, 
 }
 
 // Epilogue side of one drain: wait until the MMAs into buffer b are complete, read this warp's
-// 32 x CW slice, release the buffer, add q * 2^shl into the exact running sums.
+// 32 x CW slice, release the buffer, add q * 2^shl into the exact running sums (one 96-bit
+// two's-complement integer w2:w1:w0 per output element).
 __device__ __forceinline__ bool drain_into(Shared& sh, uint32_t tmem, int lq, int cg, int lane, uint32_t b, int shl,
-                                           uint32_t& accf_par, volatile int* abort, long long (&zlo)[CW],
-                                           long long (&zhi)[CW]) {
+                                           uint32_t& accf_par, volatile int* abort, uint32_t (&z0)[CW],
+                                           uint32_t (&z1)[CW], uint32_t (&z2)[CW]) {
   if (!mbar_wait(bar(&sh.accf[b]), (accf_par >> b) & 1u, abort)) return false;
   accf_par ^= 1u << b;
   tc_fence_after();
@@ -211,14 +212,8 @@ __device__ __forceinline__ bool drain_into(Shared& sh, uint32_t tmem, int lq, in
   tc_fence_before();
   __syncwarp();
   if (lane == 0) mbar_arrive(bar(&sh.acce[b]));
-  if (shl < 32) {
 #pragma unroll
-    for (int j = 0; j < CW; ++j) zlo[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << shl;
-  } else {
-    const int sh2 = shl - 32;
-#pragma unroll
-    for (int j = 0; j < CW; ++j) zhi[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << sh2;
-  }
+  for (int j = 0; j < CW; ++j) w96_add_shifted(z0[j], z1[j], z2[j], __float2int_rn(__uint_as_float(v[j])), shl);
   return true;
 }
 
@@ -364,13 +359,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         else crow = P->C + __ldg(P->rowdst + row) + col0;
       }
       const long long cstr = tmode ? P->ldc : 1;
-      // exact running sum Z = zhi * 2^32 + zlo; drains with shift < 32 go to zlo, the others to zhi
-      // (each part stays below 2^62 in magnitude for levels <= 8 and fewer than 2^13 groups per diagonal)
-      long long zlo[CW], zhi[CW];
+      // exact running sum per element, a 96-bit two's-complement integer z2:z1:z0 (|Z| < 2^93 for
+      // levels <= 8 and fewer than 2^13 groups per diagonal)
+      uint32_t z0[CW], z1[CW], z2[CW];
 #pragma unroll
       for (int j = 0; j < CW; ++j) {
-        zlo[j] = 0ll;
-        zhi[j] = 0ll;
+        z0[j] = 0u;
+        z1[j] = 0u;
+        z2[j] = 0u;
       }
       bool ok = true;
       // replay the issuer's schedule: buffers of k-block 0, then mid-tile drains ordered by
@@ -389,13 +385,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             gsel = g;
           }
         if (gsel < 0) break;
-        ok = drain_into(sh, tmem, lq, cg, lane, bufs[gsel], 8 * (S - 1 - gsel), accf_par, abort, zlo, zhi);
+        ok = drain_into(sh, tmem, lq, cg, lane, bufs[gsel], 8 * (S - 1 - gsel), accf_par, abort, z0, z1, z2);
         er.posted(bufs[gsel]);
         bufs[gsel] = er.next();
         nxt[gsel] += per[gsel];
       }
       for (int g = 0; g < S && ok; ++g) {
-        ok = drain_into(sh, tmem, lq, cg, lane, bufs[g], 8 * (S - 1 - g), accf_par, abort, zlo, zhi);
+        ok = drain_into(sh, tmem, lq, cg, lane, bufs[g], 8 * (S - 1 - g), accf_par, abort, z0, z1, z2);
         er.posted(bufs[g]);
       }
       if (!ok) break;
@@ -410,7 +406,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int c4 = 0; c4 < CW / ZC; ++c4) {
         if (c4 * ZC < ncol) {
 #pragma unroll
-          for (int j = 0; j < ZC; ++j) zs[lane * ZS_LD + j] = make_longlong2(zhi[c4 * ZC + j], zlo[c4 * ZC + j]);
+          for (int j = 0; j < ZC; ++j)
+            zs[lane * ZS_LD + j] = make_longlong2((long long)(((unsigned long long)z1[c4 * ZC + j] << 32) | z0[c4 * ZC + j]),
+                                                  (long long)(int)z2[c4 * ZC + j]);
           __syncwarp();
 #pragma unroll 1
           for (int j = 0; j < ZC; ++j) {
@@ -419,7 +417,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             double v = 0.0;
             if (rowok && jj < ncol) {
               const longlong2 z = zs[lane * ZS_LD + j];
-              v = z96_to_double(z.x, z.y, ea + ebj);
+              v = w96_to_double((uint32_t)z.x, (uint32_t)((unsigned long long)z.x >> 32), (uint32_t)z.y, ea + ebj);
               if (!plain) {
                 v = __dmul_rn(alpha, v);
                 if (beta != 0.0) v = __dadd_rn(v, __dmul_rn(beta, crow[jj * cstr]));
