@@ -114,19 +114,47 @@ __global__ void __launch_bounds__(256) digits_kernel(const SliceSeg* __restrict_
 #pragma unroll
     for (int q = 0; q < 8; ++q) vals[q] = (rowok && j0 + q < g.cols) ? load_src(g, i, j0 + q) : 0.0;
   }
+  int K = g.k0 + c * 8;
+  int rt = R / g.TR, rr = R % g.TR, kb = K >> KB_SHIFT, kk = K & (KB - 1);
+  long long base = (((long long)rt * g.nkb + kb) * g.S) * (long long)(g.TR * KB) + tile_off(rr, kk);
+  if constexpr (S <= 8) {
+    // Balanced base-256 digits by one add: with Y = X + sum_t 128 * 256^t (0 <= Y < 256^S because
+    // the exponent rule keeps |X| <= 127 * 256^(S-1)), byte t of Y is d + 128 for the digit of
+    // weight 256^t.  Each byte b becomes the FP16 value 1024 + b by placing it under the exponent
+    // bits 0x6400, and one half2 subtraction of 1152 leaves the digit itself, exactly.
+    constexpr unsigned long long BIAS = 0x8080808080808080ull >> (8 * (8 - S));
+    uint32_t ylo[8], yhi[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const unsigned long long Y = (unsigned long long)fixed_point64(vals[q], e, S) + BIAS;
+      ylo[q] = (uint32_t)Y;
+      yhi[q] = (uint32_t)(Y >> 32);
+    }
+    const __half2 off = __halves2half2(__float2half_rn(1152.0f), __float2half_rn(1152.0f));
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      const int bi = S - 1 - t;  // plane t holds the digit of weight 256^(S-1-t)
+      // byte bi of element 2p into byte 0 and of element 2p+1 into byte 2 (selector nibbles 0, 2)
+      const uint32_t sel = (uint32_t)((bi & 3) | (((bi & 3) + 4) << 8));
+      uint4 o;
+      uint32_t* op = reinterpret_cast<uint32_t*>(&o);
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const uint32_t a = bi < 4 ? ylo[2 * p] : yhi[2 * p], b = bi < 4 ? ylo[2 * p + 1] : yhi[2 * p + 1];
+        const uint32_t bits = (__byte_perm(a, b, sel) & 0x00FF00FFu) | 0x64006400u;
+        __half2 h = *reinterpret_cast<const __half2*>(&bits);
+        h = __hsub2(h, off);
+        op[p] = *reinterpret_cast<uint32_t*>(&h);
+      }
+      *reinterpret_cast<uint4*>(g.dst + base + (long long)t * (g.TR * KB)) = o;
+    }
+    return;
+  }
   int d[S][8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const double v = vals[q];
-    if constexpr (S <= 8) {
-      long long X = fixed_point64(v, e, S);
-#pragma unroll
-      for (int t = S - 1; t >= 0; --t) {
-        int dd = (int)((X + 128) & 255) - 128;
-        d[t][q] = dd;
-        X = (X - dd) >> 8;
-      }
-    } else {
+    {
       __int128 X = fixed_point128(v, e, S);
 #pragma unroll
       for (int t = S - 1; t >= 0; --t) {
@@ -136,9 +164,6 @@ __global__ void __launch_bounds__(256) digits_kernel(const SliceSeg* __restrict_
       }
     }
   }
-  int K = g.k0 + c * 8;
-  int rt = R / g.TR, rr = R % g.TR, kb = K >> KB_SHIFT, kk = K & (KB - 1);
-  long long base = (((long long)rt * g.nkb + kb) * g.S) * (long long)(g.TR * KB) + tile_off(rr, kk);
 #pragma unroll
   for (int t = 0; t < S; ++t) {
     __half2 h0 = __halves2half2(__int2half_rn(d[t][0]), __int2half_rn(d[t][1]));
