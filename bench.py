@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-validate", action="store_true", help="skip the |dE| check of the two-site sweep")
+    p.add_argument("--no-autotune", action="store_true", help="keep the default tile schedule")
     return p.parse_args()
 
 
@@ -305,6 +306,12 @@ def main():
     h = oz.Heff(ctx, st.m, st.n, tasks, slices=S)
     del tasks, Lbuf, Rbuf
     torch.cuda.empty_cache()
+    tuned = None
+    if not args.no_autotune:
+        (s1, s2), tms = h.autotune(psi, reps=1)
+        tuned = {"stage1": ["balanced", "balanced_asc", "strided"][s1],
+                 "stage2": ["balanced", "balanced_asc", "strided"][s2],
+                 "ms_per_schedule": [[round(a, 3), round(b, 3)] for a, b in tms]}
     info = h.info()
     y = torch.empty_like(psi)
     for _ in range(args.warmup):
@@ -413,6 +420,7 @@ def main():
         "clocks": clk,
         "validation": validation,
         "davidson": dav,
+        "autotune": tuned,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)

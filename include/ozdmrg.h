@@ -182,6 +182,14 @@ int oz_heff_info_get(const oz_heff* h, oz_heff_info* out);
  * place; synchronises the device).  info.carrier_flops follows the levels. */
 int oz_heff_set_levels(oz_heff* h, const int* s1, const int* s2);
 int oz_heff_get_levels(const oz_heff* h, int* s1, int* s2);
+/* Schedule autotuner of the grouped persistent launches (emulated handles): times every schedule
+ * of the stage tile lists over the persistent CTAs -- 0: longest first onto the least loaded CTA,
+ * each CTA's tiles in descending cost; 1: the same, ascending; 2: strided (CTA b takes tiles b,
+ * b + #CTAs, ... of the k-descending list) -- with `reps` products of d_psi each (after one
+ * warm-up product), and keeps the fastest per stage.  sched (2 ints, may be null) receives the
+ * choice for stage 1 and 2; ms (6 floats, may be null) the best stage-1 / stage-2 time of each
+ * schedule.  Synchronous.  Results do not depend on the schedule. */
+int oz_heff_autotune(oz_heff* h, const double* d_psi, int reps, int* sched, float* ms, oz_stream_t stream);
 
 /* ------------------------------------------------------------------------------------------
  * Slice-level selection per block (the precision dial of sections "Theory of emulated FP64

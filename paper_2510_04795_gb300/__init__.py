@@ -170,6 +170,15 @@ class Heff:
         b = (C.c_int * nsec)(*[int(x) for x in s2]) if s2 is not None else None
         N.check(self.lib.oz_heff_set_levels(self.h, a, b))
 
+    def autotune(self, psi: torch.Tensor, reps: int = 2, stream=None):
+        """Time every tile schedule of the two stages and keep the fastest: ((sched1, sched2),
+        [(stage-1 ms, stage-2 ms) per schedule])."""
+        _check_f64(psi)
+        sc = (C.c_int * 2)()
+        ms = (C.c_float * 6)()
+        N.check(self.lib.oz_heff_autotune(self.h, _ptr(psi), int(reps), sc, ms, _stream(stream)))
+        return (sc[0], sc[1]), [(ms[2 * c], ms[2 * c + 1]) for c in range(3)]
+
     def get_levels(self):
         nsec = len(self.m)
         a, b = (C.c_int * nsec)(), (C.c_int * nsec)()

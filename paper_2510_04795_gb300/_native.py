@@ -78,6 +78,7 @@ def load():
         "oz_heff_stage_times": (i, [vp, C.POINTER(C.c_float)]),
         "oz_heff_diag": (i, [vp, vp, vp]),
         "oz_heff_set_levels": (i, [vp, vp, vp]),
+        "oz_heff_autotune": (i, [vp, vp, i, vp, vp, vp]),
         "oz_heff_problem_features": (i, [vp, vp, vp, vp, vp]),
         "oz_heff_problem_errors": (i, [vp, vp, i, vp, vp, vp]),
         "oz_heff_select_levels": (i, [vp, vp, i, d, vp, d, vp, vp, vp]),

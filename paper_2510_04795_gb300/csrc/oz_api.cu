@@ -676,8 +676,8 @@ int oz_heff_s::prepare() {
     std::vector<GemmTile> t1 = make_tiles(p1), t2 = make_tiles(p2);
     this->nt1 = (int)t1.size();
     this->nt2 = (int)t2.size();
-    this->ht1 = t1;
-    this->ht2 = t2;
+    this->bt1 = t1;
+    this->bt2 = t2;
     if ((rc = this->alloc(&this->dF1, (size_t)(c->nsm + 1) * 4))) return rc;
     if ((rc = this->alloc(&this->dF2, (size_t)(c->nsm + 1) * 4))) return rc;
     if ((rc = this->alloc(&this->dP1, std::max<size_t>(1, p1.size()) * sizeof(GemmProblem)))) return rc;
@@ -871,11 +871,59 @@ int oz_heff_s::balance() {
   // tiles of each stage onto the persistent CTAs by cost at the current levels (the problem tables
   // on the device already hold those levels); same sizes, so the captured graph stays valid
   std::vector<int> f1, f2;
-  oz::balance_tiles(hp1, ht1, ctx->nsm, f1);
-  oz::balance_tiles(hp2, ht2, ctx->nsm, f2);
+  ht1 = bt1;
+  ht2 = bt2;
+  oz::schedule_tiles(hp1, ht1, ctx->nsm, sched1, f1);
+  oz::schedule_tiles(hp2, ht2, ctx->nsm, sched2, f2);
   if (!ht1.empty()) OZ_CU(cudaMemcpy(dT1, ht1.data(), ht1.size() * sizeof(GemmTile), cudaMemcpyHostToDevice));
   if (!ht2.empty()) OZ_CU(cudaMemcpy(dT2, ht2.data(), ht2.size() * sizeof(GemmTile), cudaMemcpyHostToDevice));
   OZ_CU(cudaMemcpy(dF1, f1.data(), f1.size() * 4, cudaMemcpyHostToDevice));
   OZ_CU(cudaMemcpy(dF2, f2.data(), f2.size() * 4, cudaMemcpyHostToDevice));
+  return OZ_OK;
+}
+
+extern "C" int oz_heff_autotune(oz_heff* h, const double* d_psi, int reps, int* sched, float* ms,
+                                oz_stream_t stream) {
+  if (!h || !d_psi) return fail(OZ_EINVAL, "null argument");
+  if (h->mode != OZ_MODE_EAGER) return fail(OZ_EINVAL, "the autotuner schedules emulated handles only");
+  if (reps < 1) return fail(OZ_EINVAL, "reps must be positive");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (int rc = h->prepare()) return rc;
+  // every schedule of both stages in turn; each product's stage times come from its events
+  OZ_CU(cudaMemcpyAsync(h->dPsi, d_psi, (size_t)h->dim * 8, cudaMemcpyDeviceToDevice, st));
+  float best[2] = {3.4e38f, 3.4e38f};
+  int pick[2] = {h->sched1, h->sched2};
+  for (int c = 0; c < oz::SCHED_COUNT; ++c) {
+    h->sched1 = c;
+    h->sched2 = c;
+    if (int rc = h->balance()) return rc;
+    float t[2] = {3.4e38f, 3.4e38f};
+    for (int r = 0; r <= reps; ++r) {  // first product warms the new tables
+      OZ_CU(cudaGraphLaunch(h->exec, st));
+      OZ_CU(cudaStreamSynchronize(st));
+      float m4[4];
+      if (int rc = oz_heff_stage_times(h, m4)) return rc;
+      if (r > 0) {
+        t[0] = std::min(t[0], m4[1]);
+        t[1] = std::min(t[1], m4[3]);
+      }
+    }
+    if (ms) {
+      ms[2 * c] = t[0];
+      ms[2 * c + 1] = t[1];
+    }
+    for (int k = 0; k < 2; ++k)
+      if (t[k] < best[k]) {
+        best[k] = t[k];
+        pick[k] = c;
+      }
+  }
+  h->sched1 = pick[0];
+  h->sched2 = pick[1];
+  if (int rc = h->balance()) return rc;
+  if (sched) {
+    sched[0] = pick[0];
+    sched[1] = pick[1];
+  }
   return OZ_OK;
 }

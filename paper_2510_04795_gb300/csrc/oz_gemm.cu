@@ -454,6 +454,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (threadIdx.x == 0 && sh.abort) atomicOr(err, 2);
 }
 
+void schedule_tiles(const std::vector<GemmProblem>& probs, std::vector<GemmTile>& tiles, int grid, int mode,
+                    std::vector<int>& first) {
+  if (mode == SCHED_STRIDED) {
+    // CTA b takes tiles b, b + grid, ... of the given order
+    std::vector<GemmTile> out;
+    out.reserve(tiles.size());
+    first.assign(grid + 1, 0);
+    for (int b = 0; b < grid; ++b) {
+      first[b] = (int)out.size();
+      for (size_t i = b; i < tiles.size(); i += grid) out.push_back(tiles[i]);
+    }
+    first[grid] = (int)out.size();
+    tiles.swap(out);
+    return;
+  }
+  balance_tiles(probs, tiles, grid, first);
+  if (mode == SCHED_BALANCED_ASC)
+    for (int b = 0; b < grid; ++b) std::reverse(tiles.begin() + first[b], tiles.begin() + first[b + 1]);
+}
+
 void balance_tiles(const std::vector<GemmProblem>& probs, std::vector<GemmTile>& tiles, int grid,
                    std::vector<int>& first) {
   // cost in MMA units: k-blocks x slice pairs, plus about 130 MMAs' worth of epilogue per tile

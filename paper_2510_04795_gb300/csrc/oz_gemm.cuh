@@ -50,5 +50,11 @@ cudaError_t launch_gemm(const GemmProblem* d_probs, const GemmTile* d_tiles, int
 // the range [first[b], first[b+1]).
 void balance_tiles(const std::vector<GemmProblem>& probs, std::vector<GemmTile>& tiles, int grid,
                    std::vector<int>& first);
+// Schedules of a tile list over `grid` CTAs: balanced (longest first, each CTA's tiles in
+// descending cost), balanced with each CTA's tiles in ascending cost, or strided (CTA b takes
+// tiles b, b + grid, ... of the given order).
+enum : int { SCHED_BALANCED = 0, SCHED_BALANCED_ASC = 1, SCHED_STRIDED = 2, SCHED_COUNT = 3 };
+void schedule_tiles(const std::vector<GemmProblem>& probs, std::vector<GemmTile>& tiles, int grid, int mode,
+                    std::vector<int>& first);
 
 }  // namespace oz

@@ -85,8 +85,10 @@ struct oz_heff_s {
   int* eB2 = nullptr;
   // problems of the two stages (host copies), the sector of each, and per-sector slice levels
   std::vector<oz::GemmProblem> hp1, hp2;
-  std::vector<oz::GemmTile> ht1, ht2;  // tile lists of the two stages (balanced per CTA)
+  std::vector<oz::GemmTile> bt1, bt2;  // tile lists of the two stages in creation order
+  std::vector<oz::GemmTile> ht1, ht2;  // the same, scheduled over the CTAs (uploaded)
   int *dF1 = nullptr, *dF2 = nullptr;  // per-CTA first tile of each stage (nsm + 1 entries)
+  int sched1 = 0, sched2 = 0;          // schedule of each stage (oz::SCHED_*), set by the autotuner
   int balance();                       // (re)assigns the tiles to CTAs for the current levels
   std::vector<int> p1sec, p2sec;
   std::vector<int> lev1, lev2;  // per source sector (stage 1), per target sector (stage 2)

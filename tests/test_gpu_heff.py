@@ -131,3 +131,18 @@ def test_heff_per_sector_levels_bitexact(ctx):
     with pytest.raises(oz.OzError):
         h.set_levels([8] * st.nsec, None)      # above the handle's level
     h.close()
+
+
+def test_heff_autotune_keeps_results(ctx):
+    """The schedule autotuner times every tile schedule and keeps the fastest per stage; the
+    product is bit-identical under every schedule."""
+    import paper_2510_04795_gb300 as oz
+    st, blocks, psi = _problem((5, 4), (8, 200), 24, False, 9)
+    h = oz.Heff(ctx, st.m, st.n, _tasks(st, blocks), slices=7)
+    y0 = h.apply(psi).clone()
+    (s1, s2), ms = h.autotune(psi, reps=2)
+    assert s1 in (0, 1, 2) and s2 in (0, 1, 2)
+    assert len(ms) == 3 and all(a > 0 and b > 0 for a, b in ms)
+    assert ms[s1][0] == min(m[0] for m in ms) and ms[s2][1] == min(m[1] for m in ms)
+    assert torch.equal(h.apply(psi), y0)
+    h.close()
