@@ -320,7 +320,8 @@ int oz_mpo_dense(const double* h1, const double* eri, int L, double* out);
  *     the largest eigenvalues (> 1e-14, at most D, never cutting through a group of equal values)
  *     of the reduced density matrix of each sector (FP64 on the device).
  *   - h1 (L x L) and eri (L^4, chemist) are HOST arrays as for oz_mpo_bond_dims.
- * Limits: a density-matrix sector may hold at most 112 states (OZ_EINVAL otherwise).
+ * Limits: a density-matrix sector may hold at most 1024 states (OZ_EINVAL otherwise; sectors of
+ * more than 112 states are diagonalised in global instead of shared memory).
  * Errors: OZ_EINVAL (arguments, limits), OZ_ENOCONV (Davidson or Jacobi did not converge),
  * OZ_ENONFINITE, OZ_ECUDA, OZ_ENOMEM.  Synchronous; uses its own stream on the context's device.
  * ------------------------------------------------------------------------------------------ */

@@ -40,6 +40,7 @@ using oz::QN;
 namespace {
 
 constexpr int EIG_MAX = 112;          // largest density-matrix sector of the on-chip eigensolver
+constexpr int EIG_MAX_GLOBAL = 1024;  // largest sector of the global-memory fallback
 constexpr int EIG_THREADS = 256;
 constexpr double LAMBDA_MIN = 1e-14;  // density-matrix eigenvalues kept must exceed this
 
@@ -147,6 +148,61 @@ __global__ void __launch_bounds__(EIG_THREADS) block_eig_kernel(const EigJob* __
     const int i = idx / m, k = idx % m;
     J.V[i * m + k] = Q[i * lda + order[k]];
   }
+}
+
+// Larger sectors (EIG_MAX < m <= EIG_MAX_GLOBAL): the same Jacobi sweeps on the matrix in global
+// memory, in place (J.A is the density matrix, overwritten; J.V receives the eigenvectors), with
+// only the rotation scratch and the ordering in shared memory.
+__global__ void __launch_bounds__(EIG_THREADS) block_eig_global_kernel(const EigJob* __restrict__ jobs,
+                                                                       int* __restrict__ info) {
+  extern __shared__ double gsm[];
+  const EigJob J = jobs[blockIdx.x];
+  const int m = J.m, h = (m + 1) / 2;
+  double* A = const_cast<double*>(J.A);
+  double* Q = J.V;
+  double* cs = gsm;
+  double* sn = cs + h;
+  double* red = sn + h;
+  int* pp = reinterpret_cast<int*>(red + 2 * (EIG_THREADS / 32));
+  int* qq = pp + h;
+  int* stop = qq + h;
+  int* order = stop + 1;
+  for (long long idx = threadIdx.x; idx < (long long)m * m; idx += blockDim.x) {
+    const int i = (int)(idx / m), j = (int)(idx % m);
+    if (i < j) {
+      const double v = 0.5 * (A[(long long)i * m + j] + A[(long long)j * m + i]);
+      A[(long long)i * m + j] = v;
+      A[(long long)j * m + i] = v;
+    }
+  }
+  __syncthreads();
+  const int sweeps = oz::jacobi_smem(A, Q, m, m, {cs, sn, pp, qq, red, stop}, 60);
+  // descending order, ties by index: the rank of every diagonal entry
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double a = A[(long long)i * m + i];
+    int r = 0;
+    for (int k = 0; k < m; ++k) {
+      const double b = A[(long long)k * m + k];
+      r += (b > a) || (b == a && k < i);
+    }
+    order[r] = i;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) info[blockIdx.x] = sweeps;
+  for (int k = threadIdx.x; k < m; k += blockDim.x) J.w[k] = A[(long long)order[k] * m + order[k]];
+  __syncthreads();
+  // columns of Q in that order: through A, which is no longer needed
+  for (long long idx = threadIdx.x; idx < (long long)m * m; idx += blockDim.x) A[idx] = Q[idx];
+  __syncthreads();
+  for (long long idx = threadIdx.x; idx < (long long)m * m; idx += blockDim.x) {
+    const int i = (int)(idx / m), k = (int)(idx % m);
+    Q[idx] = A[(long long)i * m + order[k]];
+  }
+}
+
+size_t eig_global_smem_bytes(int m) {
+  const int h = (m + 1) / 2;
+  return (size_t)(2 * h + 2 * (EIG_THREADS / 32)) * 8 + (size_t)(2 * h + 1 + m) * 4 + 64;
 }
 
 __device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
@@ -511,9 +567,9 @@ int choose_states(oz_dmrg* d, Bond& B, const double* psi, bool left, bool* keep_
   for (size_t p = 0; p < B.le.size(); ++p) {
     sec_of[p] = left ? B.le[p] : B.re[p];
     const int md = left ? B.m[p] : B.n[p];
-    if (md > EIG_MAX)
-      return oz::api_fail(OZ_EINVAL, "a density-matrix sector exceeds " + std::to_string(EIG_MAX) +
-                                         " states (on-chip eigensolver limit)");
+    if (md > EIG_MAX_GLOBAL)
+      return oz::api_fail(OZ_EINVAL, "a density-matrix sector exceeds " + std::to_string(EIG_MAX_GLOBAL) +
+                                         " states (eigensolver limit)");
     roff[p] = rtot;
     rtot += (long long)md * md;
   }
@@ -523,10 +579,10 @@ int choose_states(oz_dmrg* d, Bond& B, const double* psi, bool left, bool* keep_
   for (size_t p = 0; p < B.le.size(); ++p) wtot += left ? B.m[p] : B.n[p];
   DM_RC(d->eigw.reserve((size_t)wtot * 8));
   std::vector<GemmJob> gj;
-  std::vector<EigJob> ej;
+  std::vector<EigJob> ej, ejg;  // on-chip sectors, global-memory sectors
   std::vector<long long> woff(B.le.size());
   long long wo = 0;
-  int mmax = 1;
+  int mmax = 1, mgmax = 1;
   for (size_t p = 0; p < B.le.size(); ++p) {
     const int mp = B.m[p], np = B.n[p];
     const double* P = psi + B.psioff[p];
@@ -537,24 +593,42 @@ int choose_states(oz_dmrg* d, Bond& B, const double* psi, bool left, bool* keep_
       gj.push_back({P, P, R, np, np, mp, np, np, np, 1, 0});
     const int md = left ? mp : np;
     woff[p] = wo;
-    ej.push_back({R, (double*)d->eigw.p + wo, (double*)d->eigv.p + roff[p], md});
+    const EigJob job{R, (double*)d->eigw.p + wo, (double*)d->eigv.p + roff[p], md};
+    if (md <= EIG_MAX) {
+      ej.push_back(job);
+      mmax = std::max(mmax, md);
+    } else {
+      ejg.push_back(job);
+      mgmax = std::max(mgmax, md);
+    }
     wo += md;
-    mmax = std::max(mmax, md);
   }
   DM_RC(d->jobs.upload(gj, d->st));
   small_gemm_kernel<<<(unsigned)gj.size(), 128, 0, d->st>>>((const GemmJob*)d->jobs.p);
   DM_CU(cudaGetLastError());
   DM_CU(cudaStreamSynchronize(d->st));
-  DM_RC(d->jobs.upload(ej, d->st));
-  DM_RC(d->info.reserve(ej.size() * 4));
-  const size_t smem = eig_smem_bytes(mmax);
-  DM_CU(cudaFuncSetAttribute(block_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  block_eig_kernel<<<(unsigned)ej.size(), EIG_THREADS, smem, d->st>>>((const EigJob*)d->jobs.p, (int*)d->info.p);
-  DM_CU(cudaGetLastError());
+  // both job lists in one upload: on-chip jobs first, then the global-memory ones
+  std::vector<EigJob> all_jobs(ej);
+  all_jobs.insert(all_jobs.end(), ejg.begin(), ejg.end());
+  DM_RC(d->jobs.upload(all_jobs, d->st));
+  DM_RC(d->info.reserve(all_jobs.size() * 4));
+  if (!ej.empty()) {
+    const size_t smem = eig_smem_bytes(mmax);
+    DM_CU(cudaFuncSetAttribute(block_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    block_eig_kernel<<<(unsigned)ej.size(), EIG_THREADS, smem, d->st>>>((const EigJob*)d->jobs.p, (int*)d->info.p);
+    DM_CU(cudaGetLastError());
+  }
+  if (!ejg.empty()) {
+    const size_t smem = eig_global_smem_bytes(mgmax);
+    DM_CU(cudaFuncSetAttribute(block_eig_global_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    block_eig_global_kernel<<<(unsigned)ejg.size(), EIG_THREADS, smem, d->st>>>(
+        (const EigJob*)d->jobs.p + ej.size(), (int*)d->info.p + ej.size());
+    DM_CU(cudaGetLastError());
+  }
   std::vector<double> w(wtot);
-  std::vector<int> info(ej.size());
+  std::vector<int> info(all_jobs.size());
   DM_CU(cudaMemcpyAsync(w.data(), d->eigw.p, (size_t)wtot * 8, cudaMemcpyDeviceToHost, d->st));
-  DM_CU(cudaMemcpyAsync(info.data(), d->info.p, ej.size() * 4, cudaMemcpyDeviceToHost, d->st));
+  DM_CU(cudaMemcpyAsync(info.data(), d->info.p, all_jobs.size() * 4, cudaMemcpyDeviceToHost, d->st));
   DM_CU(cudaStreamSynchronize(d->st));
   for (int x : info)
     if (x < 0) return oz::api_fail(OZ_ENOCONV, "density-matrix Jacobi sweeps did not converge");
