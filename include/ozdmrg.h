@@ -322,7 +322,9 @@ int oz_mpo_dense(const double* h1, const double* eri, int L, double* out);
  *   - h1 (L x L) and eri (L^4, chemist) are HOST arrays as for oz_mpo_bond_dims.
  * Limits: a density-matrix sector may hold at most 1024 states (OZ_EINVAL otherwise; sectors of
  * more than 112 states are diagonalised in global instead of shared memory).
- * Errors: OZ_EINVAL (arguments, limits), OZ_ENOCONV (Davidson or Jacobi did not converge),
+ * A bond whose Davidson run stops short of its tolerance keeps its best Ritz pair and is marked
+ * in oz_dmrg_step.converged.  Errors: OZ_EINVAL (arguments, limits), OZ_ENOCONV (density-matrix
+ * Jacobi did not converge),
  * OZ_ENONFINITE, OZ_ECUDA, OZ_ENOMEM.  Synchronous; uses its own stream on the context's device.
  * ------------------------------------------------------------------------------------------ */
 typedef struct oz_dmrg_s oz_dmrg;
@@ -334,6 +336,7 @@ typedef struct oz_dmrg_step {
   int nterm;         /* MPO states on the bond: terms w of H_eff */
   int ntask;         /* sector tasks of H_eff */
   int iters;         /* Davidson iterations */
+  int converged;     /* 1 if Davidson met the tolerance (0: best Ritz pair kept, sweep continued) */
   int kept;          /* states of the new block (0: no truncation at this bond) */
   double energy;     /* lowest Ritz value */
   double discarded;  /* sum of the discarded density-matrix eigenvalues */
@@ -353,6 +356,11 @@ int oz_dmrg_steps(const oz_dmrg* d, oz_dmrg_step* out, int cap, int* n);
  * with null pointers to learn *dim. */
 int oz_dmrg_bond_heff(oz_dmrg* d, int bond, const double* d_psi, double* d_y, long long* patterns,
                       long long* dim, oz_stream_t stream);
+/* Precision of the renormalisation products E' = U^T O U of the sweep (paper, section
+ * "Theory of TNS/DMRG ...": the renormalisation is the other GEMM-heavy subroutine of the sweep).
+ * Default OZ_MODE_NATIVE (FP64 on the device); OZ_MODE_EAGER runs both passes of every bond as
+ * grouped emulated products with prec->slices digits at prec->level. */
+int oz_dmrg_set_renorm_prec(oz_dmrg* d, const oz_prec* prec);
 /* One-shot form: create, run nsweeps, destroy. */
 int dmrg_sweep(oz_ctx* ctx, const double* h1, const double* eri, int L, int nelec, int twosz, int D, int nsweeps,
                const oz_prec* prec, double davidson_tol, unsigned long long seed, double* energies);

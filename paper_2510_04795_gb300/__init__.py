@@ -338,6 +338,11 @@ class DMRG:
         except Exception:
             pass
 
+    def set_renorm(self, slices=7, level=0, mode="eager"):
+        """Precision of the renormalisation products U^T O U (default: native FP64)."""
+        p = _prec(slices, level, mode)
+        N.check(self.lib.oz_dmrg_set_renorm_prec(self.h, C.byref(p)))
+
     def run(self, nsweeps: int):
         """Runs nsweeps sweeps; returns the 2 (L - 1) nsweeps bond energies."""
         import numpy as np

@@ -40,8 +40,8 @@ class oz_heff_info(C.Structure):
 
 class oz_dmrg_step(C.Structure):
     _fields_ = [("sweep", C.c_int), ("dir", C.c_int), ("bond", C.c_int), ("dim", C.c_int), ("nterm", C.c_int),
-                ("ntask", C.c_int), ("iters", C.c_int), ("kept", C.c_int), ("energy", C.c_double),
-                ("discarded", C.c_double)]
+                ("ntask", C.c_int), ("iters", C.c_int), ("converged", C.c_int), ("kept", C.c_int),
+                ("energy", C.c_double), ("discarded", C.c_double)]
 
 
 _lib = None
@@ -105,6 +105,7 @@ def load():
         "oz_dmrg_create": (i, [vp, vp, vp, i, i, i, i, C.POINTER(oz_prec), d, C.c_ulonglong, C.POINTER(vp)]),
         "oz_dmrg_destroy": (i, [vp]),
         "oz_dmrg_run": (i, [vp, i, vp]),
+        "oz_dmrg_set_renorm_prec": (i, [vp, C.POINTER(oz_prec)]),
         "oz_dmrg_steps": (i, [vp, vp, i, C.POINTER(i)]),
         "oz_dmrg_bond_heff": (i, [vp, i, vp, vp, vp, C.POINTER(ll), vp]),
         "dmrg_sweep": (i, [vp, vp, vp, i, i, i, i, i, C.POINTER(oz_prec), d, C.c_ulonglong, vp]),

@@ -927,3 +927,85 @@ extern "C" int oz_heff_autotune(oz_heff* h, const double* d_psi, int reps, int* 
   }
   return OZ_OK;
 }
+
+namespace oz {
+int emulated_batch(oz_ctx* c, const std::vector<EmuJob>& jobs, int S, int s, cudaStream_t st) {
+  if (jobs.empty()) return OZ_OK;
+  // layout: digit planes of every A and every B, row maxima and exponents, then the tables
+  std::vector<SliceSeg> segs;
+  std::vector<GemmProblem> probs;
+  std::vector<GemmTile> tiles;
+  std::vector<long long> offA, offB, rowA, rowB;
+  long long dA = 0, dB = 0, rA = 0, rB = 0;
+  for (const EmuJob& j : jobs) {
+    if (j.M <= 0 || j.N <= 0 || j.K <= 0 || j.K > OZ_MAX_K) return fail(OZ_EINVAL, "emulated batch: bad sizes");
+    const long long nkb = cdiv(j.K, KB), nrbA = cdiv(j.M, TILE_M), nrbB = cdiv(j.N, BN);
+    offA.push_back(dA);
+    offB.push_back(dB);
+    rowA.push_back(rA);
+    rowB.push_back(rB);
+    dA += nrbA * nkb * S * TILE_M * KB;
+    dB += nrbB * nkb * S * BN * KB;
+    rA += nrbA * TILE_M;
+    rB += nrbB * BN;
+  }
+  const size_t bA = (size_t)dA * 2, bB = (size_t)dB * 2, bM = (size_t)(rA + rB) * 8, bE = (size_t)(rA + rB) * 4;
+  const size_t n = jobs.size();
+  const size_t bS = 2 * n * sizeof(SliceSeg), bP = n * sizeof(GemmProblem);
+  long long ntile = 0;
+  for (const EmuJob& j : jobs) ntile += cdiv(j.M, TILE_M) * cdiv(j.N, BN);
+  const size_t bT = (size_t)ntile * sizeof(GemmTile);
+  const size_t need = align256(bA) + align256(bB) + align256(bM) + align256(bE) + align256(bS) + align256(bP) +
+                      align256(bT) + 256;
+  if (int rc = c->reserve(need)) return rc;
+  char* p = c->ws;
+  __half* hA = (__half*)p;
+  p += align256(bA);
+  __half* hB = (__half*)p;
+  p += align256(bB);
+  unsigned long long* mx = (unsigned long long*)p;
+  p += align256(bM);
+  int* ex = (int*)p;
+  p += align256(bE);
+  SliceSeg* dSeg = (SliceSeg*)p;
+  p += align256(bS);
+  GemmProblem* dProb = (GemmProblem*)p;
+  p += align256(bP);
+  GemmTile* dTile = (GemmTile*)p;
+  long long um = 0, ud = 0;
+  for (size_t i = 0; i < n; ++i) {
+    const EmuJob& j = jobs[i];
+    const int nkb = (int)cdiv(j.K, KB);
+    SliceSeg a{};
+    a.src = j.A; a.ld = j.lda; a.rows = j.M; a.cols = j.K; a.prows = (int)(cdiv(j.M, TILE_M) * TILE_M);
+    a.pcols = nkb * KB; a.r0 = 0; a.k0 = 0; a.trans = j.transA; a.S = S; a.scale = 1.0; a.dst = hA + offA[i];
+    a.TR = TILE_M; a.nkb = nkb; a.rowmax = mx + rowA[i]; a.rowexp = ex + rowA[i]; a.unit0 = ud; a.unit0m = um;
+    ud += digit_units(a.prows, a.pcols);
+    um += rowmax_units(a.rows, a.cols);
+    SliceSeg b{};
+    b.src = j.B; b.ld = j.ldb; b.rows = j.N; b.cols = j.K; b.prows = (int)(cdiv(j.N, BN) * BN); b.pcols = nkb * KB;
+    b.r0 = 0; b.k0 = 0; b.trans = 1; b.S = S; b.scale = 1.0; b.dst = hB + offB[i]; b.TR = BN; b.nkb = nkb;
+    b.rowmax = mx + rA + rowB[i]; b.rowexp = ex + rA + rowB[i]; b.unit0 = ud; b.unit0m = um;
+    ud += digit_units(b.prows, b.pcols);
+    um += rowmax_units(b.rows, b.cols);
+    segs.push_back(a);
+    segs.push_back(b);
+    GemmProblem P{};
+    P.A = a.dst; P.B = b.dst; P.ea = a.rowexp; P.eb = b.rowexp; P.M = j.M; P.N = j.N; P.nkb = nkb;
+    P.SA = S; P.SB = S; P.s = s; P.mode = OUT_DENSE; P.C = j.C; P.ldc = j.ldc; P.alpha = 1.0; P.beta = 0.0;
+    probs.push_back(P);
+    for (int mb = 0; mb < (int)cdiv(j.M, TILE_M); ++mb)
+      for (int nb = 0; nb < (int)cdiv(j.N, BN); ++nb) tiles.push_back({(int)i, mb, nb, 0});
+  }
+  OZ_CU(cudaMemsetAsync(mx, 0, bM, st));
+  OZ_CU(cudaMemcpyAsync(dSeg, segs.data(), bS, cudaMemcpyHostToDevice, st));
+  OZ_CU(cudaMemcpyAsync(dProb, probs.data(), bP, cudaMemcpyHostToDevice, st));
+  OZ_CU(cudaMemcpyAsync(dTile, tiles.data(), bT, cudaMemcpyHostToDevice, st));
+  OZ_CU(launch_rowmax(dSeg, nullptr, (int)segs.size(), um, c->d_flags, st));
+  OZ_CU(launch_digits(dSeg, nullptr, (int)segs.size(), ud, S, st));
+  OZ_CU(launch_gemm(dProb, dTile, (int)tiles.size(), c->nsm, nullptr, s, c->d_flags + 1, st));
+  // the host tables above are read by the copies: wait before they go out of scope
+  OZ_CU(cudaStreamSynchronize(st));
+  return OZ_OK;
+}
+}  // namespace oz

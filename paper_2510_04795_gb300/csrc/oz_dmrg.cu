@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "ozdmrg.h"
+#include "oz_gemm.cuh"
 #include "oz_internal.cuh"
 #include "oz_jacobi.cuh"
 #include "oz_mpo.cuh"
@@ -325,6 +326,7 @@ struct oz_dmrg_s {
   oz_ctx* ctx = nullptr;
   int L = 0, N = 0, twosz = 0, D = 0;
   oz_prec prec{7, 0, OZ_MODE_EAGER};
+  oz_prec renorm{7, 0, OZ_MODE_NATIVE};  // precision of the renormalisation products U^T O U
   double tol = 1e-10;
   unsigned long long seed = 0;
   oz::Mpo mpo;
@@ -478,7 +480,15 @@ int project(oz_dmrg* d, const Enlarged& X, Ops& ops, bool keep_all, const std::v
       g2.push_back({U[qo], T, (double*)out->ops.mem.p + out->ops.off[w][newidx[q]], k[qo], k[q], X.b.dim[qo], k[qo],
                     k[q], k[q], 1, 0});
     }
-  if (!g1.empty()) {
+  if (!g1.empty() && d->renorm.mode == OZ_MODE_EAGER) {
+    // emulated renormalisation: both passes as grouped Ozaki products
+    std::vector<oz::EmuJob> e1, e2;
+    for (const GemmJob& g : g1) e1.push_back({g.A, g.lda, 0, g.B, g.ldb, g.C, g.ldc, g.M, g.N, g.K});
+    for (const GemmJob& g : g2) e2.push_back({g.A, g.lda, 1, g.B, g.ldb, g.C, g.ldc, g.M, g.N, g.K});
+    const int S = d->renorm.slices, lv = d->renorm.level ? d->renorm.level : d->renorm.slices;
+    DM_RC(oz::emulated_batch(d->ctx, e1, S, lv, d->st));
+    DM_RC(oz::emulated_batch(d->ctx, e2, S, lv, d->st));
+  } else if (!g1.empty()) {
     DM_RC(d->jobs.upload(g1, d->st));
     small_gemm_kernel<<<(unsigned)g1.size(), 128, 0, d->st>>>((const GemmJob*)d->jobs.p);
     DM_CU(cudaGetLastError());
@@ -739,8 +749,13 @@ int solve_bond(oz_dmrg* d, int i, int dir, int sweep, bool truncate) {
   DM_CU(cudaGetLastError());
   double E = 0.0;
   int iters = 0;
+  // a Davidson run that stops short of the tolerance (iteration limit, or a correction that
+  // vanishes because the operator is no longer symmetric to that accuracy, e.g. after coarse
+  // emulated renormalisation) still leaves its best Ritz pair: the sweep goes on with it and the
+  // step records it as not converged
   int rc = davidson_solve(B.h, (double*)psi.p, d->tol, 1000, &E, &iters, d->st);
-  if (rc != OZ_OK) return rc;
+  if (rc != OZ_OK && rc != OZ_ENOCONV) return rc;
+  const int conv = rc == OZ_OK;
   DM_RC(oz_status(d->ctx, d->st));
   oz_dmrg_step s{};
   s.sweep = sweep;
@@ -750,6 +765,7 @@ int solve_bond(oz_dmrg* d, int i, int dir, int sweep, bool truncate) {
   s.nterm = (int)B.Lw.delta.size();
   s.ntask = B.ntask;
   s.iters = iters;
+  s.converged = conv;
   s.energy = E;
   if (truncate) {
     const bool left = dir == 0;
@@ -801,6 +817,16 @@ extern "C" int oz_dmrg_create(oz_ctx* ctx, const double* h1, const double* eri, 
     return rc;
   }
   *out = d.release();
+  return OZ_OK;
+}
+
+extern "C" int oz_dmrg_set_renorm_prec(oz_dmrg* d, const oz_prec* prec) {
+  if (!d || !prec) return oz::api_fail(OZ_EINVAL, "null argument");
+  if (prec->mode != OZ_MODE_EAGER && prec->mode != OZ_MODE_NATIVE) return oz::api_fail(OZ_EINVAL, "unknown mode");
+  const int lv = prec->level ? prec->level : prec->slices;
+  if (prec->slices < 1 || prec->slices > 9 || lv < 1 || lv > prec->slices || lv > oz::MAX_LEVEL)
+    return oz::api_fail(OZ_EINVAL, "slices must be in 1..9 and the level in 1..min(S, 8)");
+  d->renorm = *prec;
   return OZ_OK;
 }
 

@@ -1,6 +1,7 @@
 // Library-internal hooks shared by the translation units of libozdmrg (not part of the C ABI).
 #pragma once
 #include <string>
+#include <vector>
 
 #include "ozdmrg.h"
 
@@ -25,6 +26,23 @@ const double* heff_diag_ptr(const oz_heff* h);
 // Synchronous (called while the caller's operator blocks are alive).
 int build_heff_diag(int nsec, const int* m, const int* n, const long long* psioff, int ntask, const oz_task* tasks,
                     double* d_diag);
+
+// A batch of independent emulated products C = op(A) B, all sliced in one pass and multiplied
+// in one grouped launch (S digits stored, level s used).  op(A) = A (M x K, row-major, lda) or,
+// with transA, the transpose of a row-major K x M matrix (lda = its row stride).  B: K x N
+// row-major (ldb); C: M x N row-major (ldc), overwritten.  Synchronous; uses the context's
+// workspace.
+struct EmuJob {
+  const double* A;
+  long long lda;
+  int transA;
+  const double* B;
+  long long ldb;
+  double* C;
+  long long ldc;
+  int M, N, K;
+};
+int emulated_batch(oz_ctx* c, const std::vector<EmuJob>& jobs, int S, int s, cudaStream_t st);
 
 // Exponent-gap histograms of the operator blocks of a new emulated handle (oz_select.cu).
 int heff_operator_hist(oz_heff* h, const oz_task* tasks);
