@@ -282,6 +282,16 @@ int davidson_ritz(oz_davidson* d, double* d_x, oz_stream_t stream);
  * not converge (d_psi and *energy then hold the last iterate). */
 int davidson_solve(oz_heff* h, double* d_psi, double tol, int max_iter, double* energy, int* iters,
                    oz_stream_t stream);
+/* Lanczos alternative to davidson_solve (paper, section "Theory of TNS/DMRG ...": the Krylov
+ * solver of the two-site update, Lanczos in most of the paper's runs): Krylov vectors with full
+ * reorthogonalisation (classical Gram-Schmidt twice), the lowest eigenpair of the tridiagonal
+ * matrix by the one-CTA Jacobi solver, explicit restart from the Ritz vector every `krylov`
+ * vectors (2..31).  Converged when the residual estimate beta_j |y_j| <= eps ("Numerical
+ * procedure": Krylov threshold epsilon).  d_psi: start vector in, normalised Ritz vector out;
+ * *energy = Ritz value, *iters = products.  OZ_ENOCONV when max_iter products (or an invariant
+ * subspace) end the run first; psi and energy then hold the last Ritz pair. */
+int lanczos_solve(oz_heff* h, double* d_psi, double eps, int max_iter, int krylov, double* energy, int* iters,
+                  oz_stream_t stream);
 /* Verification entry point of the projected eigensolver (one-CTA cyclic Jacobi, FP64): eigenvalues
  * of the symmetric m x m matrix d_G (row-major, ldg; m in 1..32) ascending into d_w[m] and the
  * eigenvectors as the columns of d_V (row-major m x m, ldv).  Synchronous.  OZ_ENOCONV if 60 sweeps
@@ -336,10 +346,12 @@ typedef struct oz_dmrg_step {
   int nterm;         /* MPO states on the bond: terms w of H_eff */
   int ntask;         /* sector tasks of H_eff */
   int iters;         /* Davidson iterations */
-  int converged;     /* 1 if Davidson met the tolerance (0: best Ritz pair kept, sweep continued) */
+  int converged;     /* 1 if the eigensolver met its tolerance (0: best Ritz pair kept, sweep continued) */
   int kept;          /* states of the new block (0: no truncation at this bond) */
   double energy;     /* lowest Ritz value */
   double discarded;  /* sum of the discarded density-matrix eigenvalues */
+  double energy_fp64;  /* with the FP64 check: psi^T H_eff psi in native FP64 (else = energy) */
+  int nonvariational;  /* with the FP64 check: 1 if energy < energy_fp64 - 1e-8 Eh */
 } oz_dmrg_step;
 int oz_dmrg_create(oz_ctx* ctx, const double* h1, const double* eri, int L, int nelec, int twosz, int D,
                    const oz_prec* prec, double davidson_tol, unsigned long long seed, oz_dmrg** out);
@@ -361,6 +373,14 @@ int oz_dmrg_bond_heff(oz_dmrg* d, int bond, const double* d_psi, double* d_y, lo
  * Default OZ_MODE_NATIVE (FP64 on the device); OZ_MODE_EAGER runs both passes of every bond as
  * grouped emulated products with prec->slices digits at prec->level. */
 int oz_dmrg_set_renorm_prec(oz_dmrg* d, const oz_prec* prec);
+/* Eigensolver of the two-site update: OZ_SOLVER_DAVIDSON (default; tol on |r|_2) or
+ * OZ_SOLVER_LANCZOS (tol = the Krylov threshold epsilon on beta_j |y_j|; Krylov dimension 30);
+ * at most 1000 products per bond.  check_fp64 = 1 re-evaluates every Ritz vector of an emulated
+ * sweep with the bond's FP64 H_eff (oz_dmrg_step.energy_fp64) and flags Ritz values below it
+ * (oz_dmrg_step.nonvariational). */
+#define OZ_SOLVER_DAVIDSON 0
+#define OZ_SOLVER_LANCZOS 1
+int oz_dmrg_set_solver(oz_dmrg* d, int solver, double tol, int check_fp64);
 /* One-shot form: create, run nsweeps, destroy. */
 int dmrg_sweep(oz_ctx* ctx, const double* h1, const double* eri, int L, int nelec, int twosz, int D, int nsweeps,
                const oz_prec* prec, double davidson_tol, unsigned long long seed, double* energies);

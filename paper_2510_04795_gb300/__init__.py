@@ -19,7 +19,7 @@ SELECTORS = {"fixed": N.OZ_SELECT_FIXED, "analytic": N.OZ_SELECT_ANALYTIC, "lear
 
 __all__ = ["Context", "Heff", "Davidson", "OzError", "ozaki_gemm", "ozaki_slice", "ozaki_slice_products",
            "heff_apply", "heff_apply_host", "heff_stage_times", "davidson_solve", "symeig_small", "DMRG",
-           "dmrg_sweep", "MLP", "OZ_NFEAT", "SELECTORS",
+           "dmrg_sweep", "MLP", "OZ_NFEAT", "SELECTORS", "lanczos_solve",
            "OZ_MODE_EAGER", "OZ_MODE_NATIVE"]
 
 
@@ -293,6 +293,19 @@ def davidson_solve(h: Heff, psi: torch.Tensor, tol: float = 1e-10, max_iter: int
     return e.value, it.value, rc
 
 
+def lanczos_solve(h: Heff, psi: torch.Tensor, eps: float = 1e-10, max_iter: int = 500, krylov: int = 30,
+                  stream=None):
+    """Lowest eigenpair by Lanczos (full reorthogonalisation, explicit restart): (energy,
+    products, status) with status OZ_OK or OZ_ENOCONV; psi is overwritten by the Ritz vector."""
+    _check_f64(psi)
+    e, it = C.c_double(), C.c_int()
+    rc = h.lib.lanczos_solve(h.h, _ptr(psi), float(eps), int(max_iter), int(krylov), C.byref(e), C.byref(it),
+                             _stream(stream))
+    if rc not in (N.OZ_OK, N.OZ_ENOCONV):
+        N.check(rc)
+    return e.value, it.value, rc
+
+
 def symeig_small(G: torch.Tensor, stream=None):
     """(eigenvalues ascending, eigenvectors as columns) of a symmetric m x m CUDA float64 matrix, m <= 32."""
     _check_f64(G)
@@ -337,6 +350,13 @@ class DMRG:
             self.close()
         except Exception:
             pass
+
+    def set_solver(self, solver="davidson", tol=1e-10, check_fp64=False):
+        """Eigensolver of the two-site update ("davidson" or "lanczos") and its tolerance;
+        check_fp64 re-evaluates every Ritz vector with the FP64 H_eff and flags non-variational
+        Ritz values in steps()."""
+        code = {"davidson": 0, "lanczos": 1}[solver]
+        N.check(self.lib.oz_dmrg_set_solver(self.h, code, float(tol), int(bool(check_fp64))))
 
     def set_renorm(self, slices=7, level=0, mode="eager"):
         """Precision of the renormalisation products U^T O U (default: native FP64)."""

@@ -41,7 +41,8 @@ class oz_heff_info(C.Structure):
 class oz_dmrg_step(C.Structure):
     _fields_ = [("sweep", C.c_int), ("dir", C.c_int), ("bond", C.c_int), ("dim", C.c_int), ("nterm", C.c_int),
                 ("ntask", C.c_int), ("iters", C.c_int), ("converged", C.c_int), ("kept", C.c_int),
-                ("energy", C.c_double), ("discarded", C.c_double)]
+                ("energy", C.c_double), ("discarded", C.c_double), ("energy_fp64", C.c_double),
+                ("nonvariational", C.c_int)]
 
 
 _lib = None
@@ -99,6 +100,7 @@ def load():
         "davidson_step": (i, [vp, C.POINTER(d), C.POINTER(d), C.POINTER(i), vp]),
         "davidson_ritz": (i, [vp, vp, vp]),
         "davidson_solve": (i, [vp, vp, d, i, C.POINTER(d), C.POINTER(i), vp]),
+        "lanczos_solve": (i, [vp, vp, d, i, i, C.POINTER(d), C.POINTER(i), vp]),
         "oz_symeig_small": (i, [vp, i, i, vp, vp, i, vp]),
         "oz_mpo_bond_dims": (i, [vp, vp, i, vp]),
         "oz_mpo_dense": (i, [vp, vp, i, vp]),
@@ -106,6 +108,7 @@ def load():
         "oz_dmrg_destroy": (i, [vp]),
         "oz_dmrg_run": (i, [vp, i, vp]),
         "oz_dmrg_set_renorm_prec": (i, [vp, C.POINTER(oz_prec)]),
+        "oz_dmrg_set_solver": (i, [vp, i, d, i]),
         "oz_dmrg_steps": (i, [vp, vp, i, C.POINTER(i)]),
         "oz_dmrg_bond_heff": (i, [vp, i, vp, vp, vp, C.POINTER(ll), vp]),
         "dmrg_sweep": (i, [vp, vp, vp, i, i, i, i, i, C.POINTER(oz_prec), d, C.c_ulonglong, vp]),

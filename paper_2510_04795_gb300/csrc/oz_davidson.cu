@@ -238,6 +238,34 @@ __global__ void __launch_bounds__(RT) normalize_kernel(const double* __restrict_
   for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n; i += stride) dst[i] = src[i] / nd;
 }
 
+// x = sum_j y[j * ystride] S_j (Ritz vector of a Krylov basis).
+__global__ void __launch_bounds__(RT) combine_kernel(VecSet Vs, int m, const double* __restrict__ y, int ystride,
+                                                     long long n, double* __restrict__ x) {
+  __shared__ double c[DMAX];
+  if (threadIdx.x < m) c[threadIdx.x] = y[threadIdx.x * ystride];
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * RT;
+  for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n; i += stride) {
+    double s = 0.0;
+    for (int j = 0; j < m; ++j) s = fma(c[j], Vs.p[j][i], s);
+    x[i] = s;
+  }
+}
+
+// Lanczos tridiagonal entries: T[j][j] = alpha, T[j][j+1] = T[j+1][j] = sqrt(beta2) (when j+1 < ld).
+__global__ void set_tri_kernel(double* __restrict__ T, int ld, int j, const double* __restrict__ alpha,
+                               const double* __restrict__ beta2, double* __restrict__ beta_out) {
+  if (threadIdx.x == 0) {
+    T[j * ld + j] = *alpha;
+    const double b = sqrt(*beta2);
+    *beta_out = b;
+    if (j + 1 < ld) {
+      T[j * ld + j + 1] = b;
+      T[(j + 1) * ld + j] = b;
+    }
+  }
+}
+
 // ---- diagonal of H_eff
 struct DiagTask {
   const double* L;
@@ -623,4 +651,89 @@ extern "C" int oz_symeig_small(const double* d_G, int m, int ldg, double* d_w, d
   if (e != cudaSuccess) return oz::api_fail(OZ_ECUDA, cudaGetErrorString(e));
   if (sweeps < 0) return oz::api_fail(OZ_ENOCONV, "Jacobi sweeps did not converge");
   return OZ_OK;
+}
+
+// Lanczos with full reorthogonalisation (classical Gram-Schmidt twice against the whole basis)
+// and explicit restart from the Ritz vector every `krylov` vectors; convergence when the
+// residual estimate beta_j |y_j| of the lowest Ritz pair is at most eps.
+extern "C" int lanczos_solve(oz_heff* h, double* d_psi, double eps, int max_iter, int krylov, double* energy,
+                             int* iters, oz_stream_t stream) {
+  if (!h || !d_psi || !energy || !iters) return oz::api_fail(OZ_EINVAL, "null argument");
+  if (max_iter < 1 || krylov < 2 || krylov > DMAX - 1 || !(eps > 0.0))
+    return oz::api_fail(OZ_EINVAL, "max_iter >= 1, krylov in 2..31 and eps > 0 required");
+  cudaStream_t st = (cudaStream_t)stream;
+  oz_davidson* d = nullptr;
+  if (int rc = oz_davidson_create(h, krylov + 1, eps, &d)) return rc;
+  struct Guard {
+    oz_davidson* d;
+    ~Guard() { oz_davidson_destroy(d); }
+  } guard{d};
+  d->vmap.clear();
+  for (int j = 0; j <= krylov; ++j) d->vmap.push_back(j);
+  double* w = d->wphys[0];
+  double* T = d->G;
+  const long long n = d->n;
+  if (int rc = d->norm_into(d_psi, d->vphys[0], DBL_MIN, st)) return rc;
+  int f = 0;
+  if (int rc = d->read_flag(st, &f)) return rc;
+  if (f) return oz::api_fail(OZ_EINVAL, "the start vector has zero or non-finite norm");
+  int total = 0, conv = 0;
+  double theta = 0.0;
+  while (true) {
+    DV_CU(cudaMemsetAsync(T, 0, (size_t)DMAX * DMAX * 8, st));
+    int j = 0;
+    bool restart = false, stop = false;
+    for (; j < krylov; ++j) {
+      if (int rc = heff_apply(h, d->vphys[j], w, stream)) return rc;
+      VecSet one{};
+      one.p[0] = d->vphys[j];
+      if (int rc = d->dots(w, one, 1, d->pA, st)) return rc;
+      reduce_kernel<<<1, RT, 0, st>>>(d->pA, d->nb, 1, d->scal + 4);  // alpha_j
+      VecSet vc = d->set(d->vphys, d->vmap, j + 1);
+      for (int pass = 0; pass < 2; ++pass) {
+        if (int rc = d->dots(w, vc, j + 1, d->pA, st)) return rc;
+        reduce_kernel<<<1, RT, 0, st>>>(d->pA, d->nb, j + 1, d->scal + 16);
+        project_out_kernel<<<d->nb, RT, 0, st>>>(w, vc, j + 1, d->scal + 16, n);
+      }
+      VecSet ww{};
+      ww.p[0] = w;
+      if (int rc = d->dots(w, ww, 1, d->pA, st)) return rc;
+      reduce_kernel<<<1, RT, 0, st>>>(d->pA, d->nb, 1, d->scal + 5);  // beta_j^2
+      set_tri_kernel<<<1, 32, 0, st>>>(T, DMAX, j, d->scal + 4, d->scal + 5, d->scal + 6);
+      symeig_kernel<<<1, RT, 0, st>>>(T, j + 1, DMAX, d->eig, d->eig + DMAX, 2, 1, d->flag + 1);
+      DV_CU(cudaGetLastError());
+      DV_CU(cudaMemcpyAsync(d->host, d->eig, 8, cudaMemcpyDeviceToHost, st));
+      DV_CU(cudaMemcpyAsync(d->host + 1, d->scal + 6, 8, cudaMemcpyDeviceToHost, st));
+      DV_CU(cudaMemcpyAsync(d->host + 2, d->eig + DMAX + 2 * j, 8, cudaMemcpyDeviceToHost, st));
+      DV_CU(cudaStreamSynchronize(st));
+      theta = d->host[0];
+      const double beta = d->host[1], est = beta * std::fabs(d->host[2]);
+      ++total;
+      if (!std::isfinite(theta) || !std::isfinite(beta))
+        return oz::api_fail(OZ_ENONFINITE, "the Lanczos recurrence produced a non-finite value");
+      if (est <= eps) {
+        conv = 1;
+        stop = true;
+      } else if (total >= max_iter || beta < 1e-14) {
+        stop = true;  // iteration limit, or an invariant subspace that still misses eps
+      } else if (j + 1 == krylov) {
+        restart = true;
+      } else {
+        // v_{j+1} = w / beta
+        normalize_kernel<<<d->nb, RT, 0, st>>>(w, d->vphys[j + 1], n, d->scal + 5, 0.0, d->flag);
+        DV_CU(cudaGetLastError());
+        continue;
+      }
+      break;
+    }
+    // Ritz vector of the basis so far: x = V y, normalised into v_0 (and into psi at the end)
+    VecSet vc = d->set(d->vphys, d->vmap, j + 1);
+    combine_kernel<<<d->nb, RT, 0, st>>>(vc, j + 1, d->eig + DMAX, 2, n, d->x);
+    DV_CU(cudaGetLastError());
+    if (int rc = d->norm_into(d->x, stop ? d_psi : d->vphys[0], DBL_MIN, st)) return rc;
+    if (stop || !restart) break;
+  }
+  *energy = theta;
+  *iters = total;
+  return conv ? OZ_OK : oz::api_fail(OZ_ENOCONV, "Lanczos stopped before its residual estimate reached eps");
 }

@@ -206,6 +206,22 @@ size_t eig_global_smem_bytes(int m) {
   return (size_t)(2 * h + 2 * (EIG_THREADS / 32)) * 8 + (size_t)(2 * h + 1 + m) * 4 + 64;
 }
 
+// Block partials of x . y (fixed order inside a block; the host adds the blocks in order).
+__global__ void dot_kernel(const double* __restrict__ x, const double* __restrict__ y, long long n,
+                           double* __restrict__ part) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s = fma(x[i], y[i], s);
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
 __device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
   // SplitMix64 (Steele, Lea and Flood, OOPSLA 2014), the published constants
   z += 0x9E3779B97F4A7C15ull;
@@ -327,6 +343,8 @@ struct oz_dmrg_s {
   int L = 0, N = 0, twosz = 0, D = 0;
   oz_prec prec{7, 0, OZ_MODE_EAGER};
   oz_prec renorm{7, 0, OZ_MODE_NATIVE};  // precision of the renormalisation products U^T O U
+  int solver = OZ_SOLVER_DAVIDSON;        // eigensolver of the two-site update
+  int check_fp64 = 0;                     // re-evaluate every Ritz vector with the FP64 H_eff
   double tol = 1e-10;
   unsigned long long seed = 0;
   oz::Mpo mpo;
@@ -505,6 +523,7 @@ int project(oz_dmrg* d, const Enlarged& X, Ops& ops, bool keep_all, const std::v
 struct Bond {
   Enlarged LE, RE;
   Ops Lw, Rw;
+  std::vector<oz_task> tasks;
   std::vector<int> le, re;            // psi sector -> LE sector, RE sector
   std::vector<long long> psioff;
   std::vector<int> m, n;
@@ -550,6 +569,7 @@ int make_bond(oz_dmrg* d, int i, Bond* B) {
       tasks.push_back({(int)p, dst, 1.0, B->Lw.ptr(w, B->le[p]), B->Rw.ptr(w, B->re[p])});
     }
   B->ntask = (int)tasks.size();
+  B->tasks = tasks;
   DM_CU(cudaStreamSynchronize(d->st));
   return oz_heff_create(d->ctx, (int)B->le.size(), B->m.data(), B->n.data(), (int)tasks.size(), tasks.data(),
                         &d->prec, &B->h);
@@ -753,9 +773,33 @@ int solve_bond(oz_dmrg* d, int i, int dir, int sweep, bool truncate) {
   // vanishes because the operator is no longer symmetric to that accuracy, e.g. after coarse
   // emulated renormalisation) still leaves its best Ritz pair: the sweep goes on with it and the
   // step records it as not converged
-  int rc = davidson_solve(B.h, (double*)psi.p, d->tol, 1000, &E, &iters, d->st);
+  int rc = d->solver == OZ_SOLVER_LANCZOS ? lanczos_solve(B.h, (double*)psi.p, d->tol, 1000, 30, &E, &iters, d->st)
+                                           : davidson_solve(B.h, (double*)psi.p, d->tol, 1000, &E, &iters, d->st);
   if (rc != OZ_OK && rc != OZ_ENOCONV) return rc;
   const int conv = rc == OZ_OK;
+  // energy of the same (normalised) vector under the FP64 H_eff of the bond: the variational
+  // reference of an emulated Ritz value
+  double E64 = E;
+  if (d->check_fp64 && d->prec.mode == OZ_MODE_EAGER) {
+    oz_prec nat{d->prec.slices, 0, OZ_MODE_NATIVE};
+    oz_heff* hn = nullptr;
+    DM_RC(oz_heff_create(d->ctx, (int)B.le.size(), B.m.data(), B.n.data(), (int)B.tasks.size(), B.tasks.data(), &nat,
+                         &hn));
+    DevBuf y, part;
+    int rc2 = y.reserve((size_t)B.dim * 8);
+    if (!rc2) rc2 = part.reserve(1024 * 8);
+    if (!rc2) rc2 = heff_apply(hn, (const double*)psi.p, (double*)y.p, d->st);
+    oz_heff_destroy(hn);
+    if (rc2) return rc2;
+    const int nb = (int)std::min<long long>(1024, (B.dim + 255) / 256);
+    dot_kernel<<<nb, 256, 0, d->st>>>((const double*)psi.p, (const double*)y.p, B.dim, (double*)part.p);
+    DM_CU(cudaGetLastError());
+    std::vector<double> ph(nb);
+    DM_CU(cudaMemcpyAsync(ph.data(), part.p, (size_t)nb * 8, cudaMemcpyDeviceToHost, d->st));
+    DM_CU(cudaStreamSynchronize(d->st));
+    E64 = 0.0;
+    for (double v : ph) E64 += v;
+  }
   DM_RC(oz_status(d->ctx, d->st));
   oz_dmrg_step s{};
   s.sweep = sweep;
@@ -767,6 +811,8 @@ int solve_bond(oz_dmrg* d, int i, int dir, int sweep, bool truncate) {
   s.iters = iters;
   s.converged = conv;
   s.energy = E;
+  s.energy_fp64 = E64;
+  s.nonvariational = E < E64 - 1e-8 ? 1 : 0;
   if (truncate) {
     const bool left = dir == 0;
     bool keep_all = false;
@@ -817,6 +863,16 @@ extern "C" int oz_dmrg_create(oz_ctx* ctx, const double* h1, const double* eri, 
     return rc;
   }
   *out = d.release();
+  return OZ_OK;
+}
+
+extern "C" int oz_dmrg_set_solver(oz_dmrg* d, int solver, double tol, int check_fp64) {
+  if (!d) return oz::api_fail(OZ_EINVAL, "null handle");
+  if (solver != OZ_SOLVER_DAVIDSON && solver != OZ_SOLVER_LANCZOS) return oz::api_fail(OZ_EINVAL, "unknown solver");
+  if (!(tol > 0.0)) return oz::api_fail(OZ_EINVAL, "tol must be positive");
+  d->solver = solver;
+  d->tol = tol;
+  d->check_fp64 = check_fp64 ? 1 : 0;
   return OZ_OK;
 }
 

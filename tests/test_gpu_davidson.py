@@ -183,3 +183,25 @@ def test_davidson_status_codes(ctx):
         oz.Davidson(h, max_sub=2)                           # subspace too small
     dv.close()
     h.close()
+
+
+@pytest.mark.parametrize("krylov", [30, 8])
+def test_lanczos_vs_oracle_and_eigh(ctx, krylov):
+    """Device Lanczos (full reorthogonalisation, explicit restarts every `krylov` vectors) against
+    dense eigh and against the oracle Lanczos on the same operator."""
+    import paper_2510_04795_gb300 as oz
+    from oracle import lanczos as olz
+    st, tasks, Lb, Rb, psi = _problem((3, 3), (3, 14), 10, False, 22)
+    H = heff.heff_dense(st, Lb, Rb)
+    lam, U = np.linalg.eigh(H)
+    h = oz.Heff(ctx, st.m, st.n, tasks, slices=7)
+    x = psi.clone()
+    e, it, rc = oz.lanczos_solve(h, x, eps=1e-10, max_iter=2000, krylov=krylov)
+    assert rc == 0
+    assert abs(e - lam[0]) <= 1e-9 * abs(lam[0])
+    xv = x.cpu().numpy()
+    assert abs(abs(xv @ U[:, 0]) - 1.0) <= 1e-9
+    th, xo, it_o, ok = olz.lanczos(lambda v: H @ v, psi.cpu().numpy(), eps=1e-10, max_iter=2000, krylov=krylov)
+    assert ok and abs(th - e) <= 1e-9 * abs(lam[0])
+    assert abs(it - it_o) <= max(3, it_o // 10)
+    h.close()

@@ -139,3 +139,26 @@ def test_emulated_renormalisation(ctx):
         d.close()
     assert dev[7] <= 1e-9
     assert dev[3] > dev[5] >= dev[7]
+
+
+def test_lanczos_sweep_and_nonvariational_flags(ctx):
+    """Lanczos as the two-site solver follows the Davidson sweep; the FP64 re-evaluation flags
+    no step at S = 7 and flags Ritz values below the FP64 energy of their vector at S = 2."""
+    import paper_2510_04795_gb300 as oz
+    L, N, D = 8, 8, 64
+    h, eri = synthetic.integrals(L, seed=0)
+    ref = oz.dmrg_sweep(ctx, h, eri, N, 0, D, 2, slices=7)
+    d = oz.DMRG(ctx, h, eri, N, 0, D, slices=7)
+    d.set_solver("lanczos", tol=1e-8, check_fp64=True)
+    e = d.run(2)
+    st = d.steps()
+    assert np.max(np.abs(e - ref)) <= 1e-6
+    assert all(s["converged"] for s in st) and not any(s["nonvariational"] for s in st)
+    assert max(abs(s["energy"] - s["energy_fp64"]) for s in st) <= 1e-9
+    d.close()
+    d = oz.DMRG(ctx, h, eri, N, 0, D, slices=7, level=2)
+    d.set_solver("lanczos", tol=1e-5, check_fp64=True)
+    d.run(1)
+    st = d.steps()
+    assert sum(s["nonvariational"] for s in st) > 0
+    d.close()
