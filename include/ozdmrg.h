@@ -373,6 +373,11 @@ int oz_dmrg_bond_heff(oz_dmrg* d, int bond, const double* d_psi, double* d_y, lo
  * Default OZ_MODE_NATIVE (FP64 on the device); OZ_MODE_EAGER runs both passes of every bond as
  * grouped emulated products with prec->slices digits at prec->level. */
 int oz_dmrg_set_renorm_prec(oz_dmrg* d, const oz_prec* prec);
+/* Precision of the reduced density matrices psi psi^T (psi^T psi on the right) that the
+ * truncation diagonalises (paper, section "Theory of TNS/DMRG ...": the truncation subroutine).
+ * Default OZ_MODE_NATIVE; OZ_MODE_EAGER forms them as grouped emulated products.  The Jacobi
+ * eigensolver itself stays FP64. */
+int oz_dmrg_set_rdm_prec(oz_dmrg* d, const oz_prec* prec);
 /* Eigensolver of the two-site update: OZ_SOLVER_DAVIDSON (default; tol on |r|_2) or
  * OZ_SOLVER_LANCZOS (tol = the Krylov threshold epsilon on beta_j |y_j|; Krylov dimension 30);
  * at most 1000 products per bond.  check_fp64 = 1 re-evaluates every Ritz vector of an emulated

@@ -358,6 +358,11 @@ class DMRG:
         code = {"davidson": 0, "lanczos": 1}[solver]
         N.check(self.lib.oz_dmrg_set_solver(self.h, code, float(tol), int(bool(check_fp64))))
 
+    def set_rdm(self, slices=7, level=0, mode="eager"):
+        """Precision of the density matrices of the truncation (default: native FP64)."""
+        p = _prec(slices, level, mode)
+        N.check(self.lib.oz_dmrg_set_rdm_prec(self.h, C.byref(p)))
+
     def set_renorm(self, slices=7, level=0, mode="eager"):
         """Precision of the renormalisation products U^T O U (default: native FP64)."""
         p = _prec(slices, level, mode)

@@ -108,6 +108,7 @@ def load():
         "oz_dmrg_destroy": (i, [vp]),
         "oz_dmrg_run": (i, [vp, i, vp]),
         "oz_dmrg_set_renorm_prec": (i, [vp, C.POINTER(oz_prec)]),
+        "oz_dmrg_set_rdm_prec": (i, [vp, C.POINTER(oz_prec)]),
         "oz_dmrg_set_solver": (i, [vp, i, d, i]),
         "oz_dmrg_steps": (i, [vp, vp, i, C.POINTER(i)]),
         "oz_dmrg_bond_heff": (i, [vp, i, vp, vp, vp, C.POINTER(ll), vp]),

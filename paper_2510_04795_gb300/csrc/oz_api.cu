@@ -984,7 +984,8 @@ int emulated_batch(oz_ctx* c, const std::vector<EmuJob>& jobs, int S, int s, cud
     um += rowmax_units(a.rows, a.cols);
     SliceSeg b{};
     b.src = j.B; b.ld = j.ldb; b.rows = j.N; b.cols = j.K; b.prows = (int)(cdiv(j.N, BN) * BN); b.pcols = nkb * KB;
-    b.r0 = 0; b.k0 = 0; b.trans = 1; b.S = S; b.scale = 1.0; b.dst = hB + offB[i]; b.TR = BN; b.nkb = nkb;
+    b.r0 = 0; b.k0 = 0; b.trans = j.transB ? 0 : 1; b.S = S; b.scale = 1.0; b.dst = hB + offB[i]; b.TR = BN;
+    b.nkb = nkb;
     b.rowmax = mx + rA + rowB[i]; b.rowexp = ex + rA + rowB[i]; b.unit0 = ud; b.unit0m = um;
     ud += digit_units(b.prows, b.pcols);
     um += rowmax_units(b.rows, b.cols);

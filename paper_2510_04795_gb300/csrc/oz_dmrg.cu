@@ -343,6 +343,7 @@ struct oz_dmrg_s {
   int L = 0, N = 0, twosz = 0, D = 0;
   oz_prec prec{7, 0, OZ_MODE_EAGER};
   oz_prec renorm{7, 0, OZ_MODE_NATIVE};  // precision of the renormalisation products U^T O U
+  oz_prec rdm{7, 0, OZ_MODE_NATIVE};     // precision of the density matrices psi psi^T
   int solver = OZ_SOLVER_DAVIDSON;        // eigensolver of the two-site update
   int check_fp64 = 0;                     // re-evaluate every Ritz vector with the FP64 H_eff
   double tol = 1e-10;
@@ -501,8 +502,8 @@ int project(oz_dmrg* d, const Enlarged& X, Ops& ops, bool keep_all, const std::v
   if (!g1.empty() && d->renorm.mode == OZ_MODE_EAGER) {
     // emulated renormalisation: both passes as grouped Ozaki products
     std::vector<oz::EmuJob> e1, e2;
-    for (const GemmJob& g : g1) e1.push_back({g.A, g.lda, 0, g.B, g.ldb, g.C, g.ldc, g.M, g.N, g.K});
-    for (const GemmJob& g : g2) e2.push_back({g.A, g.lda, 1, g.B, g.ldb, g.C, g.ldc, g.M, g.N, g.K});
+    for (const GemmJob& g : g1) e1.push_back({g.A, g.lda, 0, g.B, g.ldb, 0, g.C, g.ldc, g.M, g.N, g.K});
+    for (const GemmJob& g : g2) e2.push_back({g.A, g.lda, 1, g.B, g.ldb, 0, g.C, g.ldc, g.M, g.N, g.K});
     const int S = d->renorm.slices, lv = d->renorm.level ? d->renorm.level : d->renorm.slices;
     DM_RC(oz::emulated_batch(d->ctx, e1, S, lv, d->st));
     DM_RC(oz::emulated_batch(d->ctx, e2, S, lv, d->st));
@@ -633,10 +634,19 @@ int choose_states(oz_dmrg* d, Bond& B, const double* psi, bool left, bool* keep_
     }
     wo += md;
   }
-  DM_RC(d->jobs.upload(gj, d->st));
-  small_gemm_kernel<<<(unsigned)gj.size(), 128, 0, d->st>>>((const GemmJob*)d->jobs.p);
-  DM_CU(cudaGetLastError());
-  DM_CU(cudaStreamSynchronize(d->st));
+  if (d->rdm.mode == OZ_MODE_EAGER) {
+    // emulated density matrices: rho = psi psi^T (left) or psi^T psi (right)
+    std::vector<oz::EmuJob> ejb;
+    for (const GemmJob& g : gj)
+      ejb.push_back({g.A, g.lda, g.ta, g.B, g.ldb, g.tb, g.C, g.ldc, g.M, g.N, g.K});
+    const int lv = d->rdm.level ? d->rdm.level : d->rdm.slices;
+    DM_RC(oz::emulated_batch(d->ctx, ejb, d->rdm.slices, lv, d->st));
+  } else {
+    DM_RC(d->jobs.upload(gj, d->st));
+    small_gemm_kernel<<<(unsigned)gj.size(), 128, 0, d->st>>>((const GemmJob*)d->jobs.p);
+    DM_CU(cudaGetLastError());
+    DM_CU(cudaStreamSynchronize(d->st));
+  }
   // both job lists in one upload: on-chip jobs first, then the global-memory ones
   std::vector<EigJob> all_jobs(ej);
   all_jobs.insert(all_jobs.end(), ejg.begin(), ejg.end());
@@ -876,13 +886,28 @@ extern "C" int oz_dmrg_set_solver(oz_dmrg* d, int solver, double tol, int check_
   return OZ_OK;
 }
 
-extern "C" int oz_dmrg_set_renorm_prec(oz_dmrg* d, const oz_prec* prec) {
-  if (!d || !prec) return oz::api_fail(OZ_EINVAL, "null argument");
+namespace {
+int check_sub_prec(const oz_prec* prec) {
+  if (!prec) return oz::api_fail(OZ_EINVAL, "null argument");
   if (prec->mode != OZ_MODE_EAGER && prec->mode != OZ_MODE_NATIVE) return oz::api_fail(OZ_EINVAL, "unknown mode");
   const int lv = prec->level ? prec->level : prec->slices;
   if (prec->slices < 1 || prec->slices > 9 || lv < 1 || lv > prec->slices || lv > oz::MAX_LEVEL)
     return oz::api_fail(OZ_EINVAL, "slices must be in 1..9 and the level in 1..min(S, 8)");
+  return OZ_OK;
+}
+}  // namespace
+
+extern "C" int oz_dmrg_set_renorm_prec(oz_dmrg* d, const oz_prec* prec) {
+  if (!d) return oz::api_fail(OZ_EINVAL, "null handle");
+  DM_RC(check_sub_prec(prec));
   d->renorm = *prec;
+  return OZ_OK;
+}
+
+extern "C" int oz_dmrg_set_rdm_prec(oz_dmrg* d, const oz_prec* prec) {
+  if (!d) return oz::api_fail(OZ_EINVAL, "null handle");
+  DM_RC(check_sub_prec(prec));
+  d->rdm = *prec;
   return OZ_OK;
 }
 

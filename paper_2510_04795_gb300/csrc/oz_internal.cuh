@@ -27,17 +27,18 @@ const double* heff_diag_ptr(const oz_heff* h);
 int build_heff_diag(int nsec, const int* m, const int* n, const long long* psioff, int ntask, const oz_task* tasks,
                     double* d_diag);
 
-// A batch of independent emulated products C = op(A) B, all sliced in one pass and multiplied
+// A batch of independent emulated products C = op(A) op(B), all sliced in one pass and multiplied
 // in one grouped launch (S digits stored, level s used).  op(A) = A (M x K, row-major, lda) or,
-// with transA, the transpose of a row-major K x M matrix (lda = its row stride).  B: K x N
-// row-major (ldb); C: M x N row-major (ldc), overwritten.  Synchronous; uses the context's
-// workspace.
+// with transA, the transpose of a row-major K x M matrix (lda = its row stride); op(B) = B (K x N
+// row-major, ldb) or, with transB, the transpose of a row-major N x K matrix; C: M x N row-major
+// (ldc), overwritten.  Synchronous; uses the context's workspace.
 struct EmuJob {
   const double* A;
   long long lda;
   int transA;
   const double* B;
   long long ldb;
+  int transB;  // op(B) = the transpose of a row-major N x K matrix (ldb = its row stride)
   double* C;
   long long ldc;
   int M, N, K;
