@@ -29,8 +29,8 @@ FALLBACK_PEAK = {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gb
 
 # DRAM bytes per algorithmic carrier flop of the GEMM kernel, from one ncu capture, and the
 # digest of the kernel source it was taken on (the figure is dropped once the source changes).
-NCU_TRAFFIC = {"bytes_per_carrier_flop": 0.0021519,
-               "gemm_source_sha256": "29f2aeeff495cefeb89a9acfcf6c5273497b5a2de8e273475fcb8ffc7739ae9f"}
+NCU_TRAFFIC = {"bytes_per_carrier_flop": 0.0021553,
+               "gemm_source_sha256": "8b203552428f787137da40d4386f53a6b8e91cad1abd6d24da0c07f75289f662"}
 
 
 def parse():
