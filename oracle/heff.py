@@ -20,10 +20,14 @@ Functions:
                        every target sector one Ozaki product of the concatenated
                        intermediates with the stacked (c_k R_k)^T.  Each stage is one
                        exact emulated GEMM rounded once (see ``ozaki``).
+ * heff_entries_emulated  single entries of heff_apply_emulated from the operand rows they
+                       depend on (for sampled checks of products too large for the
+                       whole definition).
 
 Parity: heff_apply_fp64 pinned by heff_dense (brute force) and Hermiticity;
 heff_apply_emulated pinned through ``ozaki`` and by its distance to
-heff_apply_fp64 staying inside the summed per-GEMM error bounds.
+heff_apply_fp64 staying inside the summed per-GEMM error bounds;
+heff_entries_emulated pinned entry by entry against heff_apply_emulated.
 """
 from __future__ import annotations
 
@@ -126,6 +130,49 @@ def heff_apply_emulated(st, Lb: list, Rb: list, psi_flat, S: int, s: int | None 
         B2 = np.vstack([(st.term_coef[st.tasks[t][0]] * Rb[t]).T for t in ts])
         Y.append(ozaki.ozaki_gemm(A2, B2, S, s2[q]))
     return _flat(Y)
+
+
+def _row_times_sliced(a_row, eb, DB, S: int) -> np.ndarray:
+    """ozaki_gemm(a_row[None, :], B, S) for a B given by its column slicing (eb, DB) = slice_cols(B, S):
+    the same exponent rule, digits, kept pairs and single rounding as ``ozaki.ozaki_gemm``."""
+    ea, DA = ozaki.slice_rows(np.asarray(a_row, dtype=np.float64)[None, :], S)
+    P = ozaki.slice_products(DA, DB, S)
+    out = np.empty(DB[0].shape[1])
+    for j in range(out.size):
+        Z = 0
+        for (t, u), Ptu in P.items():
+            Z += int(Ptu[0, j]) * (256 ** (2 * S - t - u))
+        out[j] = ozaki.round_scaled(Z, int(ea[0]) + int(eb[j]) - 2 * (8 * S - 1))
+    return out
+
+
+def heff_entries_emulated(st, q: int, i: int, js, L_rows: dict, R_rows: dict, P_src: dict, S: int) -> np.ndarray:
+    """Entries Y[q][i, j], j in js, of heff_apply_emulated, from one row of every operand they need.
+
+    In an emulated product every row depends only on its own row of A (its own exponent) and on all
+    of B, and every entry only on its row of A and its column of B.  Hence, with the tasks t into q,
+        T_t[i, :]  = ozaki_gemm(L_t[i:i+1, :], psi[src_t])                              (stage 1)
+        Y[q][i, j] = ozaki_gemm([T_t[i, :] ...], [(c_t R_t[j, :])^T ; ...])              (stage 2)
+    are the numbers of the stacked products, whatever the order of the tasks (exact sums, maxima).
+    L_rows[t] = row i of L_t; R_rows[t] = R_t[js, :] (one row per requested j); P_src[s] = psi block
+    of source sector s.  Pinned against heff_apply_emulated entry by entry on small layouts.
+    """
+    js = list(js)
+    tasks = [t for t in range(st.ntask) if int(st.tasks[t][2]) == q]
+    sliced = {}
+    a2, b2 = [], []
+    for t in tasks:
+        k, src = int(st.tasks[t][0]), int(st.tasks[t][1])
+        if src not in sliced:
+            sliced[src] = ozaki.slice_cols(np.asarray(P_src[src], dtype=np.float64), S)
+        eb, DB = sliced[src]
+        a2.append(_row_times_sliced(L_rows[t], eb, DB, S))
+        b2.append((st.term_coef[k] * np.asarray(R_rows[t], dtype=np.float64)).T)
+    if not tasks:
+        return np.zeros(len(js))
+    A2 = np.concatenate(a2)[None, :]
+    B2 = np.vstack(b2)
+    return ozaki.ozaki_gemm(A2, B2, S)[0]
 
 
 def rel_frobenius(y, yref) -> float:

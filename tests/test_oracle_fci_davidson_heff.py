@@ -129,6 +129,28 @@ def test_heff_emulated_invariant_to_task_order():
     assert np.array_equal(y1, y2)
 
 
+@pytest.mark.parametrize("S", [3, 7])
+def test_heff_entries_match_whole_emulated_product(S):
+    # single entries from the operand rows they depend on equal the whole two-stage definition,
+    # entry by entry (spread exponents, so a wrong row or column exponent would show)
+    st, Lb, Rb, psi = _tiny_problem(seed=7)
+    y = heff.heff_apply_emulated(st, Lb, Rb, psi, S)
+    off = st.psi_offsets()
+    P = {q: psi[off[q]:off[q + 1]].reshape(int(st.m[q]), int(st.n[q])) for q in range(st.nsec)}
+    checked = 0
+    for q in range(st.nsec):
+        into = [t for t in range(st.ntask) if int(st.tasks[t][2]) == q]
+        m, n = int(st.m[q]), int(st.n[q])
+        js = list(range(n))
+        for i in range(m):
+            L_rows = {t: Lb[t][i] for t in into}
+            R_rows = {t: Rb[t][js] for t in into}
+            got = heff.heff_entries_emulated(st, q, i, js, L_rows, R_rows, P, S)
+            assert np.array_equal(got, y[off[q] + i * n: off[q] + (i + 1) * n])
+            checked += n
+    assert checked == psi.size
+
+
 def test_synthetic_bit_reproducible_blocks():
     st = synthetic.heff_structure(grid=(3, 3), dims=(2, 6), nterms=8, seed=2)
     L0, R0 = synthetic.gen_task_blocks(st, 0)
