@@ -153,6 +153,17 @@ typedef struct oz_task {
 int oz_heff_create(oz_ctx* ctx, int nsec, const int* m, const int* n, int ntask, const oz_task* tasks,
                    const oz_prec* prec, oz_heff** out);
 int oz_heff_destroy(oz_heff* h);
+/* New operator values for the same structure (paper, section "Theory of TNS/DMRG regarding error
+ * analysis": the operators change every time the environments are rebuilt, the sector structure
+ * with them only when the bond dimension does).  tasks: ntask entries with the same (src, dst) as
+ * at oz_heff_create, in the same order; coef, d_L and d_R may change (device pointers, read during
+ * the call only).  Re-slices the operators into the handle's planes (emulated) or re-copies them
+ * (native), and rebuilds the diagonal and the selector's operator statistics; allocations, tile
+ * schedules, per-sector levels and the captured graph are kept.  The next product is bit-identical
+ * to that of a handle created from the new tasks.  Synchronous (waits for products in flight).
+ * Errors: OZ_EINVAL (count or sectors differ, null pointer), OZ_ENONFINITE (NaN/Inf in a block; the
+ * handle's operators are then undefined until a successful update). */
+int oz_heff_update_ops(oz_heff* h, int ntask, const oz_task* tasks);
 /* d_y = H_eff d_psi (flat block vectors of length sum m[q] n[q]; d_y must not alias d_psi). */
 int heff_apply(oz_heff* h, const double* d_psi, double* d_y, oz_stream_t stream);
 /* End-to-end form of heff_apply on HOST vectors: copies psi_host to the device, applies H_eff,

@@ -112,6 +112,16 @@ def ozaki_slice_products(ctx: Context, A: torch.Tensor, B: torch.Tensor, slices:
     return P
 
 
+def _task_array(tasks):
+    arr = (N.oz_task * max(1, len(tasks)))()
+    for i, (s, d, c, L, R) in enumerate(tasks):
+        _check_f64(L, R)
+        if not (L.is_contiguous() and R.is_contiguous()):
+            raise OzError(N.OZ_EINVAL, "task blocks must be contiguous")
+        arr[i] = N.oz_task(int(s), int(d), float(c), _ptr(L), _ptr(R))
+    return arr
+
+
 class Heff:
     """Block-sparse two-site H_eff handle: Y = sum over tasks of coef * L psi[src] R^T into Y[dst].
 
@@ -125,12 +135,7 @@ class Heff:
         self.m = [int(x) for x in m]
         self.n = [int(x) for x in n]
         nsec = len(self.m)
-        arr = (N.oz_task * max(1, len(tasks)))()
-        for i, (s, d, c, L, R) in enumerate(tasks):
-            _check_f64(L, R)
-            if not (L.is_contiguous() and R.is_contiguous()):
-                raise OzError(N.OZ_EINVAL, "task blocks must be contiguous")
-            arr[i] = N.oz_task(int(s), int(d), float(c), _ptr(L), _ptr(R))
+        arr = _task_array(tasks)
         mm = (C.c_int * nsec)(*self.m)
         nn = (C.c_int * nsec)(*self.n)
         p = _prec(slices, level, mode)
@@ -143,6 +148,11 @@ class Heff:
         if getattr(self, "h", None) is not None and self.h.value:
             self.lib.oz_heff_destroy(self.h)
             self.h = C.c_void_p()
+
+    def update_ops(self, tasks):
+        """New coef, L and R for the same (src, dst) task list; the next product equals that of a
+        handle created from ``tasks`` (allocations, schedules, levels and graph are kept)."""
+        N.check(self.lib.oz_heff_update_ops(self.h, len(tasks), _task_array(tasks)))
 
     def __del__(self):  # pragma: no cover
         try:

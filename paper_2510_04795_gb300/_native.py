@@ -73,6 +73,7 @@ def load():
         "oz_heff_create": (i, [vp, i, C.POINTER(i), C.POINTER(i), i, C.POINTER(oz_task), C.POINTER(oz_prec),
                                C.POINTER(vp)]),
         "oz_heff_destroy": (i, [vp]),
+        "oz_heff_update_ops": (i, [vp, i, vp]),
         "heff_apply": (i, [vp, vp, vp, vp]),
         "oz_heff_info_get": (i, [vp, C.POINTER(oz_heff_info)]),
         "heff_apply_host": (i, [vp, vp, vp, vp]),

@@ -347,6 +347,82 @@ __global__ void copy_block_kernel(const double* __restrict__ src, int rows, int 
 }
 }  // namespace
 
+namespace {
+// Native path: copy every L block into the stacked stage-1 A operand and every c*R block into the
+// stacked stage-2 B^T operand (the handle's layout; asynchronous on the legacy stream).
+void native_copy_ops(const oz_heff_s* h, const oz_task* tasks) {
+  for (int t = 0; t < h->ntask; ++t) {
+    const oz_task& tk = tasks[t];
+    const int q = tk.src, d = tk.dst;
+    long long rows = h->m[d], cols = h->m[q];
+    copy_block_kernel<<<(unsigned)cdiv(rows * cols, 256), 256>>>(tk.d_L, (int)rows, (int)cols, cols, 1.0,
+                                                                h->nA1 + h->a1o[q] + h->rowin1[t] * h->m[q], h->m[q]);
+    rows = h->n[d];
+    cols = h->n[q];
+    copy_block_kernel<<<(unsigned)cdiv(rows * cols, 256), 256>>>(tk.d_R, (int)rows, (int)cols, cols, tk.coef,
+                                                                h->nB2 + h->b2o[d] + h->offk[t], h->ld2[d]);
+  }
+}
+
+// Emulated path: slice every L block into the stacked stage-1 A planes and every c*R block into the
+// stacked stage-2 B^T planes (row maxima, shared exponents, S digits), synchronously.
+int slice_ops(oz_heff_s* h, const oz_task* tasks) {
+  const int S = h->S;
+  const std::vector<int>& m = h->m;
+  const std::vector<int>& n = h->n;
+  std::vector<SliceSeg> ops;
+  ops.reserve(2 * (size_t)h->ntask);
+  long long um = 0, ud = 0;
+  for (int q = 0; q < h->nsec; ++q)
+    for (int t : h->bysrc[q]) {
+      const oz_task& tk = tasks[t];
+      SliceSeg g{};
+      g.src = tk.d_L; g.ld = m[q]; g.rows = m[tk.dst]; g.cols = m[q]; g.prows = g.rows; g.pcols = g.cols;
+      g.r0 = (int)h->rowin1[t]; g.k0 = 0; g.trans = 0; g.S = S; g.scale = 1.0;
+      g.dst = h->dA1 + h->A1off[q]; g.TR = oz::TILE_M; g.nkb = h->nkb1[q];
+      g.rowmax = h->mA1 + h->A1row[q]; g.rowexp = h->eA1 + h->A1row[q];
+      g.unit0 = ud; g.unit0m = um;
+      ud += oz::digit_units(g.prows, g.pcols);
+      um += oz::rowmax_units(g.rows, g.cols);
+      ops.push_back(g);
+    }
+  for (int q = 0; q < h->nsec; ++q)
+    for (int t : h->bydst[q]) {
+      const oz_task& tk = tasks[t];
+      SliceSeg g{};
+      g.src = tk.d_R; g.ld = n[tk.src]; g.rows = n[q]; g.cols = n[tk.src]; g.prows = g.rows; g.pcols = g.cols;
+      g.r0 = 0; g.k0 = (int)h->offk[t]; g.trans = 0; g.S = S; g.scale = tk.coef;
+      g.dst = h->dB2 + h->B2off[q]; g.TR = h->swap2[q] ? oz::TILE_M : oz::BN; g.nkb = h->nkb2[q];
+      g.rowmax = h->mB2 + h->B2row[q]; g.rowexp = h->eB2 + h->B2row[q];
+      g.unit0 = ud; g.unit0m = um;
+      ud += oz::digit_units(g.prows, g.pcols);
+      um += oz::rowmax_units(g.rows, g.cols);
+      ops.push_back(g);
+    }
+  if (ops.empty()) return OZ_OK;
+  oz_ctx* c = h->ctx;
+  OZ_CU(cudaMemset(h->mA1, 0, (size_t)h->A1row[h->nsec] * 8));
+  OZ_CU(cudaMemset(h->mB2, 0, (size_t)h->B2row[h->nsec] * 8));
+  SliceSeg* dops;
+  OZ_CU(cudaMalloc(&dops, ops.size() * sizeof(SliceSeg)));
+  cudaMemcpy(dops, ops.data(), ops.size() * sizeof(SliceSeg), cudaMemcpyHostToDevice);
+  cudaError_t e1 = oz::launch_rowmax(dops, nullptr, (int)ops.size(), um, c->d_flags, 0);
+  cudaError_t e2 = oz::launch_digits(dops, nullptr, (int)ops.size(), ud, S, 0);
+  cudaError_t e3 = cudaDeviceSynchronize();
+  cudaFree(dops);
+  if (e1 != cudaSuccess) return oz::cuda_fail(e1, "operator rowmax");
+  if (e2 != cudaSuccess) return oz::cuda_fail(e2, "operator digits");
+  if (e3 != cudaSuccess) return oz::cuda_fail(e3, "operator slicing");
+  int f[4];
+  cudaMemcpy(f, c->d_flags, 16, cudaMemcpyDeviceToHost);
+  if (f[0]) {
+    cudaMemset(c->d_flags, 0, 16);
+    return fail(OZ_ENONFINITE, "an operator block held NaN or Inf");
+  }
+  return OZ_OK;
+}
+}  // namespace
+
 extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, int ntask, const oz_task* tasks,
                               const oz_prec* prec, oz_heff** out) {
   if (!out) return fail(OZ_EINVAL, "out is null");
@@ -441,13 +517,26 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
   int rc;
   h->bytes_scratch = (long long)stoff[nsec] * 8 + 2 * h->dim * 8;
 
+  h->bysrc = std::move(bysrc);
+  h->bydst = std::move(bydst);
+  h->rows1 = rows1; h->nkb1 = nkb1; h->nkb2 = nkb2; h->ld2 = ld2;
+  h->offk = offk; h->rowin1 = rowin1; h->stoff = stoff;
+  h->A1off = A1off; h->B1off = B1off; h->A2off = A2off; h->B2off = B2off;
+  h->A1row = A1row; h->B1row = B1row; h->A2row = A2row; h->B2row = B2row;
+  h->tsrc.resize(ntask); h->tdst.resize(ntask);
+  for (int t = 0; t < ntask; ++t) { h->tsrc[t] = tasks[t].src; h->tdst[t] = tasks[t].dst; }
+
   if (mode == OZ_MODE_NATIVE) {
     if ((rc = h->alloc(&h->dPsi, (size_t)h->dim * 8))) return bail(rc);
     if ((rc = h->alloc(&h->dY, (size_t)h->dim * 8))) return bail(rc);
     if ((rc = h->alloc(&h->dStage, (size_t)stoff[nsec] * 8))) return bail(rc);
     OZ_CU(cudaMemset(h->dStage, 0, (size_t)stoff[nsec] * 8));
     // stacked FP64 copies: A1 (per source: rows1 x m[q]) and B2T (per target: n[q] x ld2, zero padded)
-    std::vector<long long> a1o(nsec + 1, 0), b2o(nsec + 1, 0), to(nsec + 1, 0);
+    std::vector<long long>& a1o = h->a1o;
+    std::vector<long long>& b2o = h->b2o;
+    std::vector<long long> to(nsec + 1, 0);
+    a1o.assign(nsec + 1, 0);
+    b2o.assign(nsec + 1, 0);
     for (int q = 0; q < nsec; ++q) {
       a1o[q + 1] = a1o[q] + (long long)rows1[q] * m[q];
       b2o[q + 1] = b2o[q] + (long long)n[q] * ld2[q];
@@ -459,24 +548,14 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
     OZ_CU(cudaMemset(h->nB2, 0, (size_t)b2o[nsec] * 8));
     h->bytes_ops = (a1o[nsec] + b2o[nsec]) * 8;
     h->bytes_scratch += to[nsec] * 8;
-    for (int t = 0; t < ntask; ++t) {
-      const oz_task& tk = tasks[t];
-      int q = tk.src, d = tk.dst;
-      long long rows = m[d], cols = m[q];
-      copy_block_kernel<<<(unsigned)cdiv(rows * cols, 256), 256>>>(tk.d_L, (int)rows, (int)cols, cols, 1.0,
-                                                                  h->nA1 + a1o[q] + rowin1[t] * m[q], m[q]);
-      rows = n[d];
-      cols = n[q];
-      copy_block_kernel<<<(unsigned)cdiv(rows * cols, 256), 256>>>(tk.d_R, (int)rows, (int)cols, cols, tk.coef,
-                                                                  h->nB2 + b2o[d] + offk[t], ld2[d]);
-    }
+    native_copy_ops(h, tasks);
     OZ_CU(cudaGetLastError());
     std::vector<long long> sc;
     sc.reserve(2 * (size_t)to[nsec]);
     for (int q = 0; q < nsec; ++q) {
-      if (bysrc[q].empty()) continue;
+      if (h->bysrc[q].empty()) continue;
       h->nat1.push_back({a1o[q], to[q], rows1[q], m[q], q});
-      for (int t : bysrc[q]) {
+      for (int t : h->bysrc[q]) {
         int d = tasks[t].dst;
         for (int i = 0; i < m[d]; ++i) {
           long long srcoff = to[q] + (rowin1[t] + i) * n[q];
@@ -490,7 +569,7 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
     if ((rc = h->alloc(&h->dScatter, sc.size() * 8))) return bail(rc);
     OZ_CU(cudaMemcpy(h->dScatter, sc.data(), sc.size() * 8, cudaMemcpyHostToDevice));
     for (int q = 0; q < nsec; ++q)
-      if (!bydst[q].empty()) h->nat2.push_back({stoff[q], b2o[q], q, ld2[q]});
+      if (!h->bydst[q].empty()) h->nat2.push_back({stoff[q], b2o[q], q, ld2[q]});
     OZ_CU(cudaDeviceSynchronize());
   } else {
     // ---- device buffers of the emulated path
@@ -501,75 +580,13 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
     OZ_CU(cudaMemset(h->dB2, 0, bB2));
     h->bytes_ops = (long long)(bA1 + bB2);
     h->bytes_scratch += (long long)(bB1 + bA2);
-    int *eA1, *eB2;
-    unsigned long long *mA1, *mB2;
-    if ((rc = h->alloc(&eA1, A1row[nsec] * 4))) return bail(rc);
-    if ((rc = h->alloc(&eB2, B2row[nsec] * 4))) return bail(rc);
-    if ((rc = h->alloc(&mA1, A1row[nsec] * 8))) return bail(rc);
-    if ((rc = h->alloc(&mB2, B2row[nsec] * 8))) return bail(rc);
-    OZ_CU(cudaMemset(mA1, 0, A1row[nsec] * 8));
-    OZ_CU(cudaMemset(mB2, 0, B2row[nsec] * 8));
-
+    if ((rc = h->alloc(&h->eA1, A1row[nsec] * 4))) return bail(rc);
+    if ((rc = h->alloc(&h->eB2, B2row[nsec] * 4))) return bail(rc);
+    if ((rc = h->alloc(&h->mA1, A1row[nsec] * 8))) return bail(rc);
+    if ((rc = h->alloc(&h->mB2, B2row[nsec] * 8))) return bail(rc);
     // ---- operator slicing (once): L blocks into A1, coef*R blocks into B2T
-    std::vector<SliceSeg> ops;
-    ops.reserve(2 * (size_t)ntask);
-    long long um = 0, ud = 0;
-    for (int q = 0; q < nsec; ++q)
-      for (int t : bysrc[q]) {
-        const oz_task& tk = tasks[t];
-        SliceSeg g{};
-        g.src = tk.d_L; g.ld = m[q]; g.rows = m[tk.dst]; g.cols = m[q]; g.prows = g.rows; g.pcols = g.cols;
-        g.r0 = (int)rowin1[t]; g.k0 = 0; g.trans = 0; g.S = S; g.scale = 1.0;
-        g.dst = h->dA1 + A1off[q]; g.TR = oz::TILE_M; g.nkb = nkb1[q];
-        g.rowmax = mA1 + A1row[q]; g.rowexp = eA1 + A1row[q];
-        g.unit0 = ud; g.unit0m = um;
-        ud += oz::digit_units(g.prows, g.pcols);
-        um += oz::rowmax_units(g.rows, g.cols);
-        ops.push_back(g);
-      }
-    for (int q = 0; q < nsec; ++q)
-      for (int t : bydst[q]) {
-        const oz_task& tk = tasks[t];
-        SliceSeg g{};
-        g.src = tk.d_R; g.ld = n[tk.src]; g.rows = n[q]; g.cols = n[tk.src]; g.prows = g.rows; g.pcols = g.cols;
-        g.r0 = 0; g.k0 = (int)offk[t]; g.trans = 0; g.S = S; g.scale = tk.coef;
-        g.dst = h->dB2 + B2off[q]; g.TR = h->swap2[q] ? oz::TILE_M : oz::BN; g.nkb = nkb2[q];
-        g.rowmax = mB2 + B2row[q]; g.rowexp = eB2 + B2row[q];
-        g.unit0 = ud; g.unit0m = um;
-        ud += oz::digit_units(g.prows, g.pcols);
-        um += oz::rowmax_units(g.rows, g.cols);
-        ops.push_back(g);
-      }
-    if (!ops.empty()) {
-      SliceSeg* dops;
-      OZ_CU(cudaMalloc(&dops, ops.size() * sizeof(SliceSeg)));
-      cudaMemcpy(dops, ops.data(), ops.size() * sizeof(SliceSeg), cudaMemcpyHostToDevice);
-      cudaError_t e1 = oz::launch_rowmax(dops, nullptr, (int)ops.size(), um, c->d_flags, 0);
-      cudaError_t e2 = oz::launch_digits(dops, nullptr, (int)ops.size(), ud, S, 0);
-      cudaError_t e3 = cudaDeviceSynchronize();
-      cudaFree(dops);
-      if (e1 != cudaSuccess) return bail(cuda_fail(e1, "operator rowmax"));
-      if (e2 != cudaSuccess) return bail(cuda_fail(e2, "operator digits"));
-      if (e3 != cudaSuccess) return bail(cuda_fail(e3, "operator slicing"));
-      int f[4];
-      cudaMemcpy(f, c->d_flags, 16, cudaMemcpyDeviceToHost);
-      if (f[0]) {
-        cudaMemset(c->d_flags, 0, 16);
-        return bail(fail(OZ_ENONFINITE, "an operator block held NaN or Inf"));
-      }
-    }
-
-    h->eA1 = eA1;
-    h->eB2 = eB2;
+    if ((rc = slice_ops(h, tasks))) return bail(rc);
   }
-  h->bysrc = std::move(bysrc);
-  h->bydst = std::move(bydst);
-  h->rows1 = rows1; h->nkb1 = nkb1; h->nkb2 = nkb2; h->ld2 = ld2;
-  h->offk = offk; h->rowin1 = rowin1; h->stoff = stoff;
-  h->A1off = A1off; h->B1off = B1off; h->A2off = A2off; h->B2off = B2off;
-  h->A1row = A1row; h->B1row = B1row; h->A2row = A2row; h->B2row = B2row;
-  h->tsrc.resize(ntask); h->tdst.resize(ntask);
-  for (int t = 0; t < ntask; ++t) { h->tsrc[t] = tasks[t].src; h->tdst[t] = tasks[t].dst; }
   for (auto& e : h->ev) OZ_CU(cudaEventCreate(&e));
   if (mode == OZ_MODE_NATIVE) h->prepared = true;
   else if (int rc2 = oz::heff_operator_hist(h, tasks)) return bail(rc2);
@@ -577,6 +594,28 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
   return OZ_OK;
 }
 
+
+extern "C" int oz_heff_update_ops(oz_heff* h, int ntask, const oz_task* tasks) {
+  if (!h) return fail(OZ_EINVAL, "handle is null");
+  if (ntask != h->ntask || (ntask > 0 && !tasks)) return fail(OZ_EINVAL, "task count differs from the handle's");
+  for (int t = 0; t < ntask; ++t) {
+    if (tasks[t].src != h->tsrc[t] || tasks[t].dst != h->tdst[t])
+      return fail(OZ_EINVAL, "task sectors differ from the handle's");
+    if (!tasks[t].d_L || !tasks[t].d_R) return fail(OZ_EINVAL, "task block pointer is null");
+  }
+  OZ_CU(cudaSetDevice(h->ctx->device));
+  OZ_CU(cudaDeviceSynchronize());  // products in flight still read the old operators
+  if (int rc = oz::build_heff_diag(h->nsec, h->m.data(), h->n.data(), h->psioff.data(), ntask, tasks, h->dDiag))
+    return rc;
+  if (h->mode == OZ_MODE_NATIVE) {
+    native_copy_ops(h, tasks);
+    OZ_CU(cudaGetLastError());
+    OZ_CU(cudaDeviceSynchronize());
+    return OZ_OK;
+  }
+  if (int rc = slice_ops(h, tasks)) return rc;
+  return oz::heff_operator_hist(h, tasks);
+}
 
 // Per-product buffers, tables, slicing segments and the CUDA graph of the emulated path.  Done on
 // the first product so that the caller can free its FP64 operator blocks after oz_heff_create.

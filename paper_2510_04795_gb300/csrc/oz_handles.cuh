@@ -83,6 +83,8 @@ struct oz_heff_s {
   std::vector<long long> offk, rowin1, stoff, A1off, B1off, A2off, B2off, A1row, B1row, A2row, B2row;
   int* eA1 = nullptr;
   int* eB2 = nullptr;
+  unsigned long long *mA1 = nullptr, *mB2 = nullptr;  // row maxima of the stacked operators
+  std::vector<long long> a1o, b2o;                    // native path: offsets of the stacked FP64 copies
   // problems of the two stages (host copies), the sector of each, and per-sector slice levels
   std::vector<oz::GemmProblem> hp1, hp2;
   std::vector<oz::GemmTile> bt1, bt2;  // tile lists of the two stages in creation order

@@ -146,3 +146,56 @@ def test_heff_autotune_keeps_results(ctx):
     assert ms[s1][0] == min(m[0] for m in ms) and ms[s2][1] == min(m[1] for m in ms)
     assert torch.equal(h.apply(psi), y0)
     h.close()
+
+
+@pytest.mark.parametrize("mode", ["eager", "native"])
+def test_heff_update_ops_equals_fresh_handle(ctx, mode):
+    """New operator values for the same structure: the product, the diagonal and (emulated) the
+    captured graph's next replay equal those of a handle created from the new values."""
+    import paper_2510_04795_gb300 as oz
+    st, blocks, psi = _problem((4, 3), (5, 70), 16, True, 2)
+    tasks_a = _tasks(st, blocks)
+    blocks_b = [synthetic.gen_task_blocks(st, t, value_seed=9, device="cuda") for t in range(st.ntask)]
+    tasks_b = [(s, d, 0.5 * c - 0.25, L, R) for (s, d, c, _, _), (L, R) in zip(tasks_a, blocks_b)]
+    h = oz.Heff(ctx, st.m, st.n, tasks_a, slices=7, mode=mode)
+    y_a = h.apply(psi).clone()
+    h.update_ops(tasks_b)
+    y_b = h.apply(psi)
+    d_b = h.diag().clone()
+    ctx.status()
+    f = oz.Heff(ctx, st.m, st.n, tasks_b, slices=7, mode=mode)
+    assert torch.equal(y_b, f.apply(psi))
+    assert torch.equal(d_b, f.diag())
+    assert not torch.equal(y_a, y_b)
+    if mode == "eager":
+        Lb = [b[0].cpu().numpy() for b in blocks_b]
+        Rb = [b[1].cpu().numpy() for b in blocks_b]
+        st_b = synthetic.HeffStructure(st.labels, st.m, st.n, st.term_delta, 0.5 * st.term_coef - 0.25, st.tasks,
+                                       st.spread, st.seed)
+        assert np.array_equal(y_b.cpu().numpy(), heff.heff_apply_emulated(st_b, Lb, Rb, psi.cpu().numpy(), 7))
+    # errors: a different task count or sector pair is refused and leaves the handle usable
+    with pytest.raises(oz.OzError):
+        h.update_ops(tasks_b[:-1])
+    s0, d0, c0, L0, R0 = tasks_b[0]
+    bad = [(d0, s0, c0, L0, R0)] + tasks_b[1:] if s0 != d0 else None
+    if bad is not None:
+        with pytest.raises(oz.OzError):
+            h.update_ops(bad)
+    assert torch.equal(h.apply(psi), y_b)
+    h.close()
+    f.close()
+
+
+def test_heff_update_ops_nonfinite(ctx):
+    import paper_2510_04795_gb300 as oz
+    st, blocks, psi = _problem((3, 3), (2, 20), 8, False, 1)
+    tasks = _tasks(st, blocks)
+    h = oz.Heff(ctx, st.m, st.n, tasks, slices=5)
+    y = h.apply(psi).clone()
+    Lbad = tasks[0][3].clone()
+    Lbad.view(-1)[0] = float("nan")
+    with pytest.raises(oz.OzError):
+        h.update_ops([(tasks[0][0], tasks[0][1], tasks[0][2], Lbad, tasks[0][4])] + tasks[1:])
+    h.update_ops(tasks)
+    assert torch.equal(h.apply(psi), y)
+    h.close()
