@@ -117,6 +117,27 @@ def gemm_source_digest() -> str:
     return h.hexdigest()
 
 
+def slice_t_bytes(st, S: int):
+    """Bytes the slicing of the intermediate T moves per product: the FP64 staging rows of every
+    target sector (K padded as the library pads it) read once, and S FP16-carried digit planes of
+    those rows written once (the tile padding rows are zero from allocation and never rewritten)."""
+    import numpy as np
+    cd = lambda a, b: -(-a // b)
+    m, n, T = st.m.astype(np.int64), st.n.astype(np.int64), st.tasks
+    k2 = np.zeros(st.nsec, dtype=np.int64)
+    for _, src, dst in T:
+        k2[dst] += cd(int(n[src]), 8) * 8
+    rd = wr = 0
+    for q in range(st.nsec):
+        if k2[q] == 0:
+            continue
+        ld2 = cd(int(k2[q]), 16) * 16
+        mq = int(m[q])
+        rd += 8 * mq * ld2
+        wr += 2 * S * mq * ld2
+    return rd, wr
+
+
 def structure(args):
     import synthetic
     cfg = dict(synthetic.CONFIGS[args.config])
@@ -368,6 +389,13 @@ def main():
             "algorithmic": f"s(s+1)/2 * sum_tasks 2(m'mn+m'nn') = {P}*{F:.4e} flop per step over 2 launches",
             "peak_source": f"bf16_tflops_sustained ({pk_src}); fp16 and bf16 share the nominal rate"}
 
+    rd, wr = slice_t_bytes(st, S)
+    hbm_peak = float(pk.get("hbm_gbs", FALLBACK_PEAK["hbm_gbs"]))
+    hbm_ach = (rd + wr) / (stage[2] * 1e-3) / 1e9
+    hbm = {"kernel": f"oz::digits_kernel<{S}> (slicing of the intermediate T)", "achieved": hbm_ach,
+           "peak": hbm_peak, "unit": "GB/s", "frac": hbm_ach / hbm_peak, "bytes_read": rd, "bytes_written": wr,
+           "peak_source": f"hbm_gbs ({pk_src})"}
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         from oracle import heff as OH
@@ -411,6 +439,7 @@ def main():
                 "d2h_bytes_per_step": int(psi.numel() * 8), "matches_device_result": ok_e2e},
         "gpu_launches": 5 * args.steps,
         "roofline": roof,
+        "hbm": hbm,
         "cpu_baseline": cpu,
         "native_fp64": native,
         "rel_frobenius_vs_native_fp64": rel_native,
