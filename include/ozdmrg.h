@@ -53,11 +53,12 @@ extern "C" {
 /* precision / dispatch of a product */
 #define OZ_MODE_EAGER 0    /* every product emulated (the paper's eager mode) */
 #define OZ_MODE_NATIVE 1   /* native FP64 (cuBLAS DGEMM, emulation off) on the same task list */
+#define OZ_MODE_PERFORMANT 2 /* ozaki_gemm only: the faster of the two for the shape (paper's performant mode) */
 
 typedef struct oz_prec {
   int slices; /* S: digits stored per value, 1..9 */
   int level;  /* s: digits used, 1..min(S, 8); 0 means s = S */
-  int mode;   /* OZ_MODE_EAGER or OZ_MODE_NATIVE */
+  int mode;   /* OZ_MODE_EAGER or OZ_MODE_NATIVE (OZ_MODE_PERFORMANT: ozaki_gemm only) */
 } oz_prec;
 
 typedef void* oz_stream_t; /* a cudaStream_t (0 = legacy default stream) */
@@ -82,12 +83,22 @@ int oz_status(oz_ctx* ctx, oz_stream_t stream);
  *   A: m x k (lda >= k), B: k x n (ldb >= n), C: m x n (ldc >= n); all device, row-major.
  *   alpha*c and beta*C are each rounded to FP64 and then added (no fused multiply-add).
  *   prec->mode == OZ_MODE_NATIVE runs cuBLAS DGEMM instead.
+ *   prec->mode == OZ_MODE_PERFORMANT (paper, section "Numerical procedure": emulation only where it
+ *   pays off) runs whichever of the two was faster for this shape class: the first call whose
+ *   (ceil log2 m, ceil log2 n, ceil log2 k, S, s) is new times both paths on the caller's A and B
+ *   into a scratch C (synchronising the stream, allocating m x n doubles), caches the winner in the
+ *   context and then runs it; later calls of the class run the cached choice.  The result is that
+ *   of the chosen path (bit-exact emulation or cuBLAS DGEMM).  Not for use under stream capture.
  * Errors: OZ_EINVAL for negative sizes, short leading dimensions, slices outside 1..9 or a level
  * outside 1..min(S,8).  May grow the context workspace (cudaMalloc, synchronous): call it once
  * outside stream capture before capturing.
  * ------------------------------------------------------------------------------------------ */
 int ozaki_gemm(oz_ctx* ctx, int m, int n, int k, double alpha, const double* d_A, int lda, const double* d_B,
                int ldb, double beta, double* d_C, int ldc, const oz_prec* prec, oz_stream_t stream);
+/* The choice OZ_MODE_PERFORMANT made for the shape class of (m, n, k) at prec's S and level:
+ * *mode = OZ_MODE_EAGER or OZ_MODE_NATIVE, or -1 if no call of that class has been timed yet;
+ * ms (2 floats, may be null) receives the timed emulated and native durations. */
+int oz_performant_choice(oz_ctx* ctx, int m, int n, int k, const oz_prec* prec, int* mode, float* ms);
 
 /* ------------------------------------------------------------------------------------------
  * ozaki_gemm_noalloc: the same emulated product as ozaki_gemm (bit-identical results) for callers

@@ -17,7 +17,7 @@ from ._native import OzError, OZ_MODE_EAGER, OZ_MODE_NATIVE, OZ_NFEAT
 
 SELECTORS = {"fixed": N.OZ_SELECT_FIXED, "analytic": N.OZ_SELECT_ANALYTIC, "learned": N.OZ_SELECT_LEARNED}
 
-__all__ = ["Context", "Heff", "Davidson", "OzError", "ozaki_gemm", "ozaki_slice", "ozaki_slice_products",
+__all__ = ["Context", "Heff", "Davidson", "OzError", "ozaki_gemm", "performant_choice", "ozaki_slice", "ozaki_slice_products",
            "heff_apply", "heff_apply_host", "heff_stage_times", "davidson_solve", "symeig_small", "DMRG",
            "dmrg_sweep", "MLP", "OZ_NFEAT", "SELECTORS", "lanczos_solve",
            "OZ_MODE_EAGER", "OZ_MODE_NATIVE"]
@@ -34,7 +34,7 @@ def _stream(stream) -> C.c_void_p:
 
 
 def _prec(slices: int, level: int, mode) -> N.oz_prec:
-    m = {"eager": OZ_MODE_EAGER, "native": OZ_MODE_NATIVE}.get(mode, mode)
+    m = {"eager": OZ_MODE_EAGER, "native": OZ_MODE_NATIVE, "performant": N.OZ_MODE_PERFORMANT}.get(mode, mode)
     return N.oz_prec(int(slices), int(level), int(m))
 
 
@@ -88,6 +88,17 @@ def ozaki_gemm(ctx: Context, A: torch.Tensor, B: torch.Tensor, C_out: torch.Tens
                                max(B.stride(0), 1), float(beta), _ptr(C_out), max(C_out.stride(0), 1),
                                C.byref(p), _stream(stream)))
     return C_out
+
+
+def performant_choice(ctx: Context, m: int, n: int, k: int, slices=7, level=0):
+    """(mode, emulated ms, native ms) that ``mode="performant"`` chose for the shape class of
+    (m, n, k); mode is "eager", "native" or None when no call of that class has run yet."""
+    p = _prec(slices, level, "eager")
+    md = C.c_int()
+    ms = (C.c_float * 2)()
+    N.check(ctx.lib.oz_performant_choice(ctx.h, int(m), int(n), int(k), C.byref(p), C.byref(md), ms))
+    name = {OZ_MODE_EAGER: "eager", OZ_MODE_NATIVE: "native"}.get(md.value)
+    return name, ms[0], ms[1]
 
 
 def ozaki_slice(ctx: Context, A: torch.Tensor, slices: int, stream=None):

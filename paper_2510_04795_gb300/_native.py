@@ -11,7 +11,7 @@ import os
 _LIBPATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libozdmrg.so")
 
 OZ_OK, OZ_EINVAL, OZ_ENONFINITE, OZ_ENOCONV, OZ_EVARIATIONAL, OZ_ETIMEOUT, OZ_ECUDA, OZ_ENOMEM = range(8)
-OZ_MODE_EAGER, OZ_MODE_NATIVE = 0, 1
+OZ_MODE_EAGER, OZ_MODE_NATIVE, OZ_MODE_PERFORMANT = 0, 1, 2
 OZ_NFEAT = 20
 OZ_SELECT_FIXED, OZ_SELECT_ANALYTIC, OZ_SELECT_LEARNED = 0, 1, 2
 STATUS_NAMES = {0: "OZ_OK", 1: "OZ_EINVAL", 2: "OZ_ENONFINITE", 3: "OZ_ENOCONV", 4: "OZ_EVARIATIONAL",
@@ -67,6 +67,7 @@ def load():
         "oz_last_error": (C.c_char_p, []),
         "oz_status": (i, [vp, vp]),
         "ozaki_gemm": (i, [vp, i, i, i, d, vp, i, vp, i, d, vp, i, C.POINTER(oz_prec), vp]),
+        "oz_performant_choice": (i, [vp, i, i, i, C.POINTER(oz_prec), C.POINTER(i), C.POINTER(C.c_float)]),
         "ozaki_slice": (i, [vp, i, i, vp, i, i, vp, vp, vp]),
         "ozaki_gemm_noalloc": (i, [i, i, i, d, vp, i, vp, i, d, vp, i, i, i, vp]),
         "ozaki_slice_products": (i, [vp, i, i, i, vp, i, vp, i, i, vp, vp]),

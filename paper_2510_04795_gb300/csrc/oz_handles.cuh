@@ -4,6 +4,7 @@
 #include <cublas_v2.h>
 
 #include <algorithm>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -25,6 +26,9 @@ struct oz_ctx_s {
   size_t ws_bytes = 0;
   int* d_flags = nullptr;  // [0] non-finite input, [1] kernel timeout/abort
   cublasHandle_t cublas = nullptr;
+  // performant dispatch of ozaki_gemm: shape class -> (chosen mode, emulated ms, native ms)
+  struct PerfChoice { int mode; float ms_emu, ms_nat; };
+  std::map<unsigned long long, PerfChoice> perf;
 
   // bump allocation inside the workspace (grown with cudaMalloc when too small)
   int reserve(size_t bytes) {

@@ -3,6 +3,7 @@ import numpy as np
 import pytest
 import torch
 
+import synthetic
 from oracle import ozaki
 
 pytestmark = pytest.mark.gpu
@@ -183,3 +184,42 @@ def test_gemm_extreme_exponents(ctx, scale_a, scale_b):
         ctx.status()
         ref = ozaki.ozaki_gemm(A, B, S)
         assert np.array_equal(C.view(np.int64), ref.view(np.int64))
+
+
+def test_performant_mode_dispatch(ctx):
+    """Performant mode: each shape class is timed once both ways, the faster path runs, and the
+    result is that path's, bit for bit; beta * C stays intact through the timing runs."""
+    import paper_2510_04795_gb300 as oz
+    g = torch.Generator(device="cuda").manual_seed(5)
+    # tiny product: a cuBLAS DGEMM launch beats slicing plus the emulated GEMM
+    A = torch.randn(32, 24, generator=g, device="cuda", dtype=torch.float64)
+    B = torch.randn(24, 40, generator=g, device="cuda", dtype=torch.float64)
+    C0 = torch.randn(32, 40, generator=g, device="cuda", dtype=torch.float64)
+    assert oz.performant_choice(ctx, 32, 40, 24)[0] is None
+    C = C0.clone()
+    oz.ozaki_gemm(ctx, A, B, C, alpha=0.5, beta=2.0, mode="performant")
+    mode, t_emu, t_nat = oz.performant_choice(ctx, 32, 40, 24)
+    assert mode in ("eager", "native") and t_emu > 0 and t_nat > 0
+    assert mode == ("eager" if t_emu <= t_nat else "native")
+    ref = C0.clone()
+    oz.ozaki_gemm(ctx, A, B, ref, alpha=0.5, beta=2.0, mode=mode)
+    assert torch.equal(C, ref)
+    # a second call of the same class (different sizes inside it) reuses the choice
+    A2, B2 = A[:30, :20].contiguous(), B[:20, :33].contiguous()
+    C2 = oz.ozaki_gemm(ctx, A2, B2, mode="performant")
+    assert oz.performant_choice(ctx, 30, 33, 20)[1:] == (t_emu, t_nat)
+    assert torch.equal(C2, oz.ozaki_gemm(ctx, A2, B2, mode=mode))
+    # a large product: FP64 runs far below the emulated rate, so emulation is chosen
+    A = torch.randn(4096, 4096, generator=g, device="cuda", dtype=torch.float64)
+    B = torch.randn(4096, 4096, generator=g, device="cuda", dtype=torch.float64)
+    C = oz.ozaki_gemm(ctx, A, B, mode="performant")
+    mode, t_emu, t_nat = oz.performant_choice(ctx, 4096, 4096, 4096)
+    assert mode == "eager" and t_emu < t_nat
+    assert torch.equal(C, oz.ozaki_gemm(ctx, A, B, mode="eager"))
+    ctx.status()
+    # other entry points keep rejecting the mode
+    st = synthetic.heff_structure(grid=(2, 2), dims=(2, 6), nterms=4, seed=1)
+    blocks = [synthetic.gen_task_blocks(st, t, device="cuda") for t in range(st.ntask)]
+    tasks = [(int(s), int(d), float(st.term_coef[k]), L, R) for (k, s, d), (L, R) in zip(st.tasks, blocks)]
+    with pytest.raises(oz.OzError):
+        oz.Heff(ctx, st.m, st.n, tasks, slices=7, mode="performant")
