@@ -433,7 +433,9 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+        "dtype_note": "tensor-core arithmetic on INT8-valued digits carried in FP16, exact integer accumulation "
+                      "(FP32 groups, 96-bit sums), one rounding to FP64 per output; inputs and outputs FP64",
         "config": dict(workload_config(args, st, cfg), parallelism=f"replicas x{world}"),
         "e2e": {"value": world * F / (ms_e2e * 1e-3) / 1e12, "unit": UNIT, "h2d_bytes_per_step": int(psi.numel() * 8),
                 "d2h_bytes_per_step": int(psi.numel() * 8), "matches_device_result": ok_e2e},
