@@ -374,10 +374,18 @@ typedef struct oz_dmrg_step {
   double discarded;  /* sum of the discarded density-matrix eigenvalues */
   double energy_fp64;  /* with the FP64 check: psi^T H_eff psi in native FP64 (else = energy) */
   int nonvariational;  /* with the FP64 check: 1 if energy < energy_fp64 - 1e-8 Eh */
+  int predicted;       /* 1 if the eigensolver started from the previous bond's transformed solution */
 } oz_dmrg_step;
 int oz_dmrg_create(oz_ctx* ctx, const double* h1, const double* eri, int L, int nelec, int twosz, int D,
                    const oz_prec* prec, double davidson_tol, unsigned long long seed, oz_dmrg** out);
 int oz_dmrg_destroy(oz_dmrg* d);
+/* Start vectors of the two-site eigensolver (on by default): the previous bond's solution carried
+ * to this bond -- the same vector at a turning point (unchanged problem), otherwise the truncated
+ * side rotated into the new block (U^T psi or psi U) and the other block's states expanded over
+ * (site x block) with the kept vectors that made that block in the previous sweep.  Where no
+ * prediction applies (the first pass over the reference blocks) or its squared norm is below 1e-6, a
+ * seeded random vector is used, as with on = 0.  Converged energies do not depend on the start. */
+int oz_dmrg_set_prediction(oz_dmrg* d, int on);
 /* Runs nsweeps more sweeps; energies (if not null) receives 2 (L - 1) nsweeps Ritz values in
  * bond order. */
 int oz_dmrg_run(oz_dmrg* d, int nsweeps, double* energies);

@@ -372,6 +372,10 @@ class DMRG:
         except Exception:
             pass
 
+    def set_prediction(self, on: bool = True):
+        """Start each bond's eigensolver from the previous bond's transformed solution (default)."""
+        N.check(self.lib.oz_dmrg_set_prediction(self.h, 1 if on else 0))
+
     def set_solver(self, solver="davidson", tol=1e-10, check_fp64=False):
         """Eigensolver of the two-site update ("davidson" or "lanczos") and its tolerance;
         check_fp64 re-evaluates every Ritz vector with the FP64 H_eff and flags non-variational

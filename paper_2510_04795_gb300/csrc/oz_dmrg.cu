@@ -327,10 +327,19 @@ struct Ops {
   const double* ptr(int w, int in) const { return (const double*)mem.p + off[w][in]; }
 };
 
-// Environment = operators of a block on its own basis.
+// Environment = operators of a block on its own basis, and how that basis came out of the
+// truncation of an enlarged basis `src` (absent for the start's reference blocks): every state kept
+// (ident), or per src sector q the new sector newidx[q] (-1: dropped) spanned by k[q] kept vectors,
+// row-major src.b.dim[q] x k[q] at U + uoff[q].  The kept vectors carry a two-site vector from one
+// bond to the next (the start of the next eigensolver run).
 struct Env {
   Basis basis;
   Ops ops;
+  bool has_src = false, ident = false;
+  Enlarged src;
+  std::vector<int> k, newidx;
+  std::vector<long long> uoff;
+  DevBuf U;
 };
 
 }  // namespace
@@ -355,6 +364,17 @@ struct oz_dmrg_s {
   std::vector<oz_dmrg_step> steps;
   long long nsolve = 0;
   DevBuf jobs, groups, work, eigw, eigv, rho, info;
+  // the last two-site solution and its layout (start-vector prediction of the next bond)
+  int predict = 1;
+  struct Prev {
+    bool valid = false, truncated = false;
+    int bond = -1, dir = 0;
+    long long dim = 0;
+    std::vector<int> le, re, m, n;
+    std::vector<long long> psioff;
+    Enlarged LE, RE;
+  } prev;
+  DevBuf prev_psi, pred_tmp, pred_jobs;
   QN target() const { return {N, twosz}; }
 };
 
@@ -447,6 +467,9 @@ int build_ops(oz_dmrg* d, const Env& E, const Enlarged& X, int site, bool left, 
 int project(oz_dmrg* d, const Enlarged& X, Ops& ops, bool keep_all, const std::vector<const double*>& U,
             const std::vector<int>& k, const std::vector<std::vector<long long>>& pats, Env* out) {
   const int nsec = (int)X.b.q.size();
+  out->has_src = true;
+  out->src = X;
+  out->ident = keep_all;
   if (keep_all) {
     out->basis = X.b;
     out->ops.delta = ops.delta;
@@ -466,6 +489,21 @@ int project(oz_dmrg* d, const Enlarged& X, Ops& ops, bool keep_all, const std::v
       out->basis.dim.push_back(k[q]);
       out->basis.pat.push_back(pats[q]);
     }
+  // keep the kept vectors (the eigenvector arena is reused by the next truncation)
+  out->k = k;
+  out->newidx = newidx;
+  out->uoff.assign(nsec, -1);
+  long long ut = 0;
+  for (int q = 0; q < nsec; ++q)
+    if (k[q] > 0) {
+      out->uoff[q] = ut;
+      ut += (long long)X.b.dim[q] * k[q];
+    }
+  DM_RC(out->U.reserve((size_t)std::max(ut, 1ll) * 8));
+  for (int q = 0; q < nsec; ++q)
+    if (k[q] > 0)
+      DM_CU(cudaMemcpyAsync((double*)out->U.p + out->uoff[q], U[q], (size_t)X.b.dim[q] * k[q] * 8,
+                            cudaMemcpyDeviceToDevice, d->st));
   const int nst = (int)ops.delta.size(), nn = (int)out->basis.q.size();
   out->ops.delta = ops.delta;
   out->ops.out.assign(nst, std::vector<int>(nn, -1));
@@ -768,15 +806,177 @@ int init_environments(oz_dmrg* d) {
   return OZ_OK;
 }
 
+// Start vector of bond i from the previous bond's solution (White's transformation of the two-site
+// vector): at a turning point the same problem (the vector itself); after a left-to-right step
+// psi' = U_L^T psi, with the right block's states expanded over (site i+1 block) by the vectors
+// that made that block; after a right-to-left step the mirror image.  Returns *ok = false when no
+// prediction applies (first pass, reference blocks); the caller then draws a random start.
+int predict_start(oz_dmrg* d, int i, int dir, const Bond& B, double* psi, bool* ok) {
+  *ok = false;
+  const auto& P = d->prev;
+  if (!d->predict || !P.valid) return OZ_OK;
+  if (P.bond == i && !P.truncated && P.le == B.le && P.re == B.re && P.m == B.m && P.n == B.n) {
+    DM_CU(cudaMemcpyAsync(psi, d->prev_psi.p, (size_t)B.dim * 8, cudaMemcpyDeviceToDevice, d->st));
+    *ok = true;
+    return OZ_OK;
+  }
+  if (!P.truncated || P.dir != dir || P.bond != (dir == 0 ? i - 1 : i + 1)) return OZ_OK;
+  // T: the truncated side of the previous vector; X: the block whose states are expanded
+  const Env* T = dir == 0 ? d->left[i].get() : d->right[i + 1].get();
+  const Env* X = dir == 0 ? d->right[i].get() : d->left[i + 1].get();
+  if (!T || !X || !T->has_src || !X->has_src) return OZ_OK;
+  const Enlarged& Bx = dir == 0 ? B.RE : B.LE;  // the new enlarged basis X's states are expanded over
+  if (X->src.b.q.size() != Bx.b.q.size() || X->src.b.dim != Bx.b.dim) return OZ_OK;
+  // new psi sector of (LE sector, RE sector)
+  auto psi_sector = [&](int le, int re) {
+    for (size_t p = 0; p < B.le.size(); ++p)
+      if (B.le[p] == le && B.re[p] == re) return (int)p;
+    return -1;
+  };
+  // inverse of X's sector map: X sector -> src (= Bx) sector
+  std::vector<int> xsrc(X->basis.q.size(), -1);
+  for (size_t q = 0; q < X->src.b.q.size(); ++q) {
+    const int nq = X->ident ? (int)q : X->newidx[q];
+    if (nq >= 0) xsrc[nq] = (int)q;
+  }
+  const double* Tsrc = (const double*)d->prev_psi.p;
+  const int np = (int)P.le.size();
+  // step 1: the truncated side, one product per previous block (or the block itself when all states
+  // were kept): tmp_p = U^T psi_p (left) or psi_p U (right)
+  std::vector<long long> toff(np, -1);
+  std::vector<int> trows(np, 0), tcols(np, 0), tsec(np, -1);
+  long long tt = 0;
+  for (int p = 0; p < np; ++p) {
+    const int q = dir == 0 ? P.le[p] : P.re[p];
+    const int nq = T->ident ? q : T->newidx[q];
+    if (nq < 0) continue;
+    tsec[p] = nq;
+    trows[p] = dir == 0 ? (T->ident ? P.m[p] : T->k[q]) : P.m[p];
+    tcols[p] = dir == 0 ? P.n[p] : (T->ident ? P.n[p] : T->k[q]);
+    toff[p] = tt;
+    tt += (long long)trows[p] * tcols[p];
+  }
+  DM_RC(d->pred_tmp.reserve((size_t)std::max(tt, 1ll) * 8));
+  double* tmp = (double*)d->pred_tmp.p;
+  std::vector<GemmJob> g1, g2;
+  for (int p = 0; p < np; ++p) {
+    if (toff[p] < 0) continue;
+    const int q = dir == 0 ? P.le[p] : P.re[p];
+    const double* src = Tsrc + P.psioff[p];
+    if (T->ident) {
+      DM_CU(cudaMemcpyAsync(tmp + toff[p], src, (size_t)P.m[p] * P.n[p] * 8, cudaMemcpyDeviceToDevice, d->st));
+    } else if (dir == 0) {
+      // k x n = (m x k)^T (m x n)
+      g1.push_back({(const double*)T->U.p + T->uoff[q], src, tmp + toff[p], trows[p], tcols[p], P.m[p], T->k[q],
+                    P.n[p], tcols[p], 1, 0});
+    } else {
+      // m x k = (m x n) (n x k)
+      g1.push_back({src, (const double*)T->U.p + T->uoff[q], tmp + toff[p], trows[p], tcols[p], P.n[p], P.n[p],
+                    T->k[q], tcols[p], 0, 0});
+    }
+  }
+  // step 2: the other side's block states expanded over (site x block) of the new bond
+  DM_CU(cudaMemsetAsync(psi, 0, (size_t)B.dim * 8, d->st));
+  const Enlarged& Pold = dir == 0 ? P.RE : P.LE;  // the previous enlarged basis holding X's states
+  const Enlarged& Bt = dir == 0 ? B.LE : B.RE;    // the new enlarged basis holding the truncated side
+  for (int p = 0; p < np; ++p) {
+    if (toff[p] < 0) continue;
+    const int r = dir == 0 ? P.re[p] : P.le[p];
+    for (size_t a = 0; a < Pold.sec.size(); ++a)
+      for (int sg = 0; sg < 4; ++sg) {
+        if (Pold.sec[a][sg] != r) continue;
+        const int xs = xsrc[a];                                  // Bx sector the states of a came from
+        const int ts = Bt.sec[tsec[p]][sg];                      // sector of (truncated side, site) piece
+        if (xs < 0 || ts < 0) continue;
+        const int pn = dir == 0 ? psi_sector(ts, xs) : psi_sector(xs, ts);
+        if (pn < 0) continue;
+        const int da = X->basis.dim[a];
+        const long long poff = Pold.off[a][sg];
+        const long long boff = Bt.off[tsec[p]][sg];
+        double* dst = psi + B.psioff[pn];
+        if (dir == 0) {
+          // rows boff.. of the new block (n columns = Bx dim of xs) = tmp[:, poff..poff+da] V^T
+          double* C = dst + boff * B.n[pn];
+          const double* A = tmp + toff[p] + poff;
+          if (X->ident)
+            DM_CU(cudaMemcpy2DAsync(C, (size_t)B.n[pn] * 8, A, (size_t)tcols[p] * 8, (size_t)da * 8, trows[p],
+                                    cudaMemcpyDeviceToDevice, d->st));
+          else
+            g2.push_back({A, (const double*)X->U.p + X->uoff[xs], C, trows[p], B.n[pn], da, tcols[p], da, B.n[pn], 0,
+                          1});
+        } else {
+          // columns boff.. of the new block (m rows = Bx dim of xs) = W tmp[poff..poff+da, :]
+          double* C = dst + boff;
+          const double* Bm = tmp + toff[p] + poff * tcols[p];
+          if (X->ident)
+            DM_CU(cudaMemcpy2DAsync(C, (size_t)B.n[pn] * 8, Bm, (size_t)tcols[p] * 8, (size_t)tcols[p] * 8, da,
+                                    cudaMemcpyDeviceToDevice, d->st));
+          else
+            g2.push_back({(const double*)X->U.p + X->uoff[xs], Bm, C, B.m[pn], tcols[p], da, da, tcols[p], B.n[pn], 0,
+                          0});
+        }
+      }
+  }
+  if (!g1.empty()) {
+    DM_RC(d->pred_jobs.upload(g1, d->st));
+    small_gemm_kernel<<<(unsigned)g1.size(), 128, 0, d->st>>>((const GemmJob*)d->pred_jobs.p);
+    DM_CU(cudaGetLastError());
+    DM_CU(cudaStreamSynchronize(d->st));  // the job table is reused below
+  }
+  if (!g2.empty()) {
+    DM_RC(d->pred_jobs.upload(g2, d->st));
+    small_gemm_kernel<<<(unsigned)g2.size(), 128, 0, d->st>>>((const GemmJob*)d->pred_jobs.p);
+    DM_CU(cudaGetLastError());
+  }
+  // a usable start has a finite norm well away from zero (the discarded weight is small)
+  DevBuf part;
+  DM_RC(part.reserve(1024 * 8));
+  const int nb = (int)std::min<long long>(1024, (B.dim + 255) / 256);
+  dot_kernel<<<nb, 256, 0, d->st>>>(psi, psi, B.dim, (double*)part.p);
+  DM_CU(cudaGetLastError());
+  std::vector<double> ph(nb);
+  DM_CU(cudaMemcpyAsync(ph.data(), part.p, (size_t)nb * 8, cudaMemcpyDeviceToHost, d->st));
+  DM_CU(cudaStreamSynchronize(d->st));
+  double nrm = 0.0;
+  for (double v : ph) nrm += v;
+  *ok = std::isfinite(nrm) && nrm > 1e-6;
+  return OZ_OK;
+}
+
+// The solution of bond i (its Ritz vector in psi) as the source of the next prediction.
+int remember(oz_dmrg* d, int i, int dir, bool truncated, const Bond& B, const double* psi) {
+  auto& P = d->prev;
+  P.valid = false;
+  DM_RC(d->prev_psi.reserve((size_t)B.dim * 8));
+  DM_CU(cudaMemcpyAsync(d->prev_psi.p, psi, (size_t)B.dim * 8, cudaMemcpyDeviceToDevice, d->st));
+  P.bond = i;
+  P.dir = dir;
+  P.truncated = truncated;
+  P.dim = B.dim;
+  P.le = B.le;
+  P.re = B.re;
+  P.m = B.m;
+  P.n = B.n;
+  P.psioff = B.psioff;
+  P.LE = B.LE;
+  P.RE = B.RE;
+  P.valid = true;
+  return OZ_OK;
+}
+
 int solve_bond(oz_dmrg* d, int i, int dir, int sweep, bool truncate) {
   Bond B;
   DM_RC(make_bond(d, i, &B));
   DevBuf psi;
   DM_RC(psi.reserve((size_t)B.dim * 8));
   const unsigned long long key = d->seed * 0x2545F4914F6CDD1Dull + (unsigned long long)(++d->nsolve);
-  random_vector_kernel<<<(unsigned)std::min<long long>(1024, (B.dim + 255) / 256), 256, 0, d->st>>>(
-      (double*)psi.p, B.dim, key);
-  DM_CU(cudaGetLastError());
+  bool predicted = false;
+  DM_RC(predict_start(d, i, dir, B, (double*)psi.p, &predicted));
+  if (!predicted) {
+    random_vector_kernel<<<(unsigned)std::min<long long>(1024, (B.dim + 255) / 256), 256, 0, d->st>>>(
+        (double*)psi.p, B.dim, key);
+    DM_CU(cudaGetLastError());
+  }
   double E = 0.0;
   int iters = 0;
   // a Davidson run that stops short of the tolerance (iteration limit, or a correction that
@@ -823,6 +1023,7 @@ int solve_bond(oz_dmrg* d, int i, int dir, int sweep, bool truncate) {
   s.energy = E;
   s.energy_fp64 = E64;
   s.nonvariational = E < E64 - 1e-8 ? 1 : 0;
+  s.predicted = predicted ? 1 : 0;
   if (truncate) {
     const bool left = dir == 0;
     bool keep_all = false;
@@ -838,6 +1039,7 @@ int solve_bond(oz_dmrg* d, int i, int dir, int sweep, bool truncate) {
     if (left) d->left[i + 1] = std::move(Env_);
     else d->right[i] = std::move(Env_);
   }
+  DM_RC(remember(d, i, dir, truncate, B, (const double*)psi.p));
   d->steps.push_back(s);
   return OZ_OK;
 }
@@ -873,6 +1075,12 @@ extern "C" int oz_dmrg_create(oz_ctx* ctx, const double* h1, const double* eri, 
     return rc;
   }
   *out = d.release();
+  return OZ_OK;
+}
+
+extern "C" int oz_dmrg_set_prediction(oz_dmrg* d, int on) {
+  if (!d) return oz::api_fail(OZ_EINVAL, "null handle");
+  d->predict = on ? 1 : 0;
   return OZ_OK;
 }
 

@@ -183,3 +183,28 @@ def test_emulated_density_matrices(ctx):
             assert np.max(np.abs(e - ref)) <= 1e-9
         assert np.all(e >= e_fci - 1e-9)
         assert e[-1] - e_fci < 5e-3
+
+
+def test_predicted_starts_same_energies_fewer_iterations(ctx):
+    """Start vectors carried from bond to bond: the energies of random starts at every bond (both
+    solve to a 1e-10 residual), every solve after the first left-to-right pass predicted (in that
+    pass too wherever the right block records how it was made), and far fewer Davidson iterations."""
+    import paper_2510_04795_gb300 as oz
+    L, N, D = 8, 8, 64
+    h, eri = synthetic.integrals(L, seed=0)
+    runs = {}
+    for pred in (False, True):
+        d = oz.DMRG(ctx, h, eri, N, 0, D)
+        d.set_prediction(pred)
+        e = d.run(4)
+        runs[pred] = (e, d.steps())
+        d.close()
+    (e0, s0), (e1, s1) = runs[False], runs[True]
+    assert np.max(np.abs(e1 - e0)) < 1e-8
+    assert not any(s["predicted"] for s in s0)
+    # the first solve has nothing to start from; after the first pass every solve is predicted
+    assert not s1[0]["predicted"]
+    assert all(s["predicted"] for s in s1[L - 1:])
+    it0, it1 = sum(s["iters"] for s in s0), sum(s["iters"] for s in s1)
+    print("Davidson iterations, random starts:", it0, "predicted starts:", it1)
+    assert it1 < 0.6 * it0
