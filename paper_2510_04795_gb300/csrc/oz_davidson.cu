@@ -119,10 +119,16 @@ __global__ void __launch_bounds__(RT) gram_kernel(const double* __restrict__ pA,
 // Eigenpairs of a symmetric m x m matrix (m <= 32) by the one-CTA cyclic Jacobi solver of
 // oz_jacobi.cuh.  Eigenvalues ascending into w[0..m); the first nvec eigenvectors into V (row-major
 // m x nvec, leading dimension ldv).  info[0] = number of sweeps (-1: not converged).
+// Warm start (Qin, qin_m > 0): when the matrix is the previous one (qin_m x qin_m, diagonalised by
+// the orthogonal Qin) bordered by new rows and columns, Jacobi starts from A = W^T G W with
+// W = Qin (+) identity -- diagonal but for the border -- and accumulates its rotations onto W, so a
+// subspace that grows by one vector per iteration needs one or two sweeps instead of a full solve.
+// Qout (may alias Qin; leading dimension DMAX) receives all m eigenvectors, unsorted.
 __global__ void __launch_bounds__(RT) symeig_kernel(const double* __restrict__ Gin, int m, int ldg,
                                                     double* __restrict__ w, double* __restrict__ V, int ldv,
-                                                    int nvec, int* __restrict__ info) {
-  __shared__ double A[DMAX][DMAX + 1], Q[DMAX][DMAX + 1];
+                                                    int nvec, int* __restrict__ info, const double* Qin = nullptr,
+                                                    int qin_m = 0, double* Qout = nullptr) {
+  __shared__ double A[DMAX][DMAX + 1], Q[DMAX][DMAX + 1], Tm[DMAX][DMAX + 1];
   __shared__ double cs[DMAX / 2], sn[DMAX / 2];
   __shared__ int pp[DMAX / 2], qq[DMAX / 2];
   __shared__ double red[2 * (RT / 32)];
@@ -133,8 +139,38 @@ __global__ void __launch_bounds__(RT) symeig_kernel(const double* __restrict__ G
     int i = idx / m, j = idx % m;
     A[i][j] = 0.5 * (Gin[i * ldg + j] + Gin[j * ldg + i]);
   }
+  const bool warm = Qin != nullptr && qin_m > 0 && qin_m <= m;
+  if (warm) {
+    for (int idx = tid; idx < m * m; idx += RT) {
+      const int i = idx / m, j = idx % m;
+      Q[i][j] = (i < qin_m && j < qin_m) ? Qin[i * DMAX + j] : (i == j ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < m * m; idx += RT) {  // Tm = G W
+      const int i = idx / m, j = idx % m;
+      double acc = 0.0;
+      for (int k = 0; k < m; ++k) acc = fma(A[i][k], Q[k][j], acc);
+      Tm[i][j] = acc;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < m * m; idx += RT) {  // A = W^T Tm
+      const int i = idx / m, j = idx % m;
+      double acc = 0.0;
+      for (int k = 0; k < m; ++k) acc = fma(Q[k][i], Tm[k][j], acc);
+      A[i][j] = acc;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < m * m; idx += RT) {  // symmetric to the last bit
+      const int i = idx / m, j = idx % m;
+      Tm[i][j] = 0.5 * (A[i][j] + A[j][i]);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < m * m; idx += RT) A[idx / m][idx % m] = Tm[idx / m][idx % m];
+  }
   __syncthreads();
-  const int sweeps = oz::jacobi_smem(&A[0][0], &Q[0][0], DMAX + 1, m, {cs, sn, pp, qq, red, &stop}, MAX_SWEEPS);
+  const int sweeps =
+      oz::jacobi_smem(&A[0][0], &Q[0][0], DMAX + 1, m, {cs, sn, pp, qq, red, &stop}, MAX_SWEEPS, !warm,
+                      warm ? 1e-18 : 0.0);
   oz::jacobi_order(&A[0][0], DMAX + 1, m, false, order);
   if (tid == 0) info[0] = sweeps;
   for (int i = tid; i < m; i += RT) w[i] = A[order[i]][order[i]];
@@ -143,6 +179,8 @@ __global__ void __launch_bounds__(RT) symeig_kernel(const double* __restrict__ G
     const int i = idx / nv, k = idx % nv;
     V[i * ldv + k] = Q[i][order[k]];
   }
+  if (Qout)
+    for (int idx = tid; idx < m * m; idx += RT) Qout[(idx / m) * DMAX + idx % m] = Q[idx / m][idx % m];
 }
 
 // Ritz vector, residual and preconditioned correction in one pass (y = first eigenvector of the
@@ -391,6 +429,8 @@ struct oz_davidson_s {
   std::vector<double*> vphys, wphys;  // physical slots
   std::vector<int> vmap, wmap;        // logical subspace vector -> physical slot
   double *x = nullptr, *G = nullptr, *eig = nullptr, *pA = nullptr, *pB = nullptr, *scal = nullptr;
+  double* Qw = nullptr;  // eigenvectors of the last projected matrix (warm start of the next one)
+  int qw_m = 0;          // its order (0: none)
   int* flag = nullptr;  // [0] breakdown / bad norm, [1] Jacobi sweeps
   double* host = nullptr;  // page-locked: theta, theta1, |r|^2, flag
   int m = 0;
@@ -462,7 +502,7 @@ extern "C" int oz_davidson_create(oz_heff* h, int max_sub, double tol, oz_davids
   d->tol = tol;
   const int nslot = max_sub + 3;
   const size_t vec = (size_t)d->ldn * 8;
-  const size_t small = (size_t)DMAX * DMAX * 8 + (size_t)DMAX * 3 * 8 + 2 * (size_t)DMAX * d->nb * 8 + 64 * 8 + 64;
+  const size_t small = 2 * (size_t)DMAX * DMAX * 8 + (size_t)DMAX * 3 * 8 + 2 * (size_t)DMAX * d->nb * 8 + 64 * 8 + 64;
   const size_t total = (2 * (size_t)nslot + 1) * vec + small + 1024;
   cudaError_t e = cudaMalloc(&d->mem, total);
   if (e != cudaSuccess) {
@@ -481,6 +521,8 @@ extern "C" int oz_davidson_create(oz_heff* h, int max_sub, double tol, oz_davids
   d->x = (double*)p;
   p += vec;
   d->G = (double*)p;
+  p += (size_t)DMAX * DMAX * 8;
+  d->Qw = (double*)p;
   p += (size_t)DMAX * DMAX * 8;
   d->eig = (double*)p;
   p += (size_t)DMAX * 3 * 8;
@@ -518,6 +560,7 @@ extern "C" int davidson_start(oz_davidson* d, const double* d_x0, oz_stream_t st
   d->vmap.assign(1, 0);
   d->wmap.assign(1, 0);
   d->m = 1;
+  d->qw_m = 0;
   d->started = d->converged = false;
   d->iters = 0;
   DV_CU(cudaMemsetAsync(d->flag, 0, 8, st));
@@ -544,8 +587,12 @@ extern "C" int davidson_step(oz_davidson* d, double* theta, double* resid, int* 
   const int m = d->m;
   d->iters += 1;
   // lowest eigenpairs of the projected matrix, Ritz vector, residual, correction
-  symeig_kernel<<<1, RT, 0, st>>>(d->G, m, DMAX, d->eig, d->eig + DMAX, 2, 2, d->flag + 1);
+  // the subspace grew by one vector since the last solve unless it was restarted: warm start
+  const bool warm = d->qw_m > 0 && d->qw_m == m - 1;
+  symeig_kernel<<<1, RT, 0, st>>>(d->G, m, DMAX, d->eig, d->eig + DMAX, 2, 2, d->flag + 1, warm ? d->Qw : nullptr,
+                                  warm ? d->qw_m : 0, d->Qw);
   DV_CU(cudaGetLastError());
+  d->qw_m = m;
   const int fd = d->free_slot(d->vmap, {});
   VecSet vs = d->set(d->vphys, d->vmap, m), ws = d->set(d->wphys, d->wmap, m);
   ritz_kernel<<<d->nb, RT, 0, st>>>(vs, ws, m, d->eig, oz::heff_diag_ptr(d->h), d->n, d->x, d->vphys[fd], d->pA);
@@ -576,6 +623,7 @@ extern "C" int davidson_step(oz_davidson* d, double* theta, double* resid, int* 
     d->vmap = {a, b};
     d->wmap = {wa, wb};
     d->m = 2;
+    d->qw_m = 0;  // a new basis: the next projected matrix is solved from scratch
     if (int rc = d->gram(0, st)) return rc;
     if (int rc = d->gram(1, st)) return rc;
   }
@@ -681,6 +729,7 @@ extern "C" int lanczos_solve(oz_heff* h, double* d_psi, double eps, int max_iter
   double theta = 0.0;
   while (true) {
     DV_CU(cudaMemsetAsync(T, 0, (size_t)DMAX * DMAX * 8, st));
+    d->qw_m = 0;
     int j = 0;
     bool restart = false, stop = false;
     for (; j < krylov; ++j) {
@@ -700,8 +749,12 @@ extern "C" int lanczos_solve(oz_heff* h, double* d_psi, double eps, int max_iter
       if (int rc = d->dots(w, ww, 1, d->pA, st)) return rc;
       reduce_kernel<<<1, RT, 0, st>>>(d->pA, d->nb, 1, d->scal + 5);  // beta_j^2
       set_tri_kernel<<<1, 32, 0, st>>>(T, DMAX, j, d->scal + 4, d->scal + 5, d->scal + 6);
-      symeig_kernel<<<1, RT, 0, st>>>(T, j + 1, DMAX, d->eig, d->eig + DMAX, 2, 1, d->flag + 1);
+      // T grows by one row and column per step: warm start from the last solve's eigenvectors
+      const bool warm = d->qw_m > 0 && d->qw_m == j;
+      symeig_kernel<<<1, RT, 0, st>>>(T, j + 1, DMAX, d->eig, d->eig + DMAX, 2, 1, d->flag + 1,
+                                      warm ? d->Qw : nullptr, warm ? d->qw_m : 0, d->Qw);
       DV_CU(cudaGetLastError());
+      d->qw_m = j + 1;
       DV_CU(cudaMemcpyAsync(d->host, d->eig, 8, cudaMemcpyDeviceToHost, st));
       DV_CU(cudaMemcpyAsync(d->host + 1, d->scal + 6, 8, cudaMemcpyDeviceToHost, st));
       DV_CU(cudaMemcpyAsync(d->host + 2, d->eig + DMAX + 2 * j, 8, cudaMemcpyDeviceToHost, st));

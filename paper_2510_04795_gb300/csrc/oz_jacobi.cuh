@@ -25,14 +25,20 @@ __device__ __forceinline__ double jacobi_warp_sum(double v) {
 }
 
 // A: m x m symmetric (element (i, j) at A[i * lda + j]), overwritten by its diagonalised form;
-// Q (same layout) receives the eigenvectors as columns.  Every thread of the CTA must call it.
-// Returns the number of sweeps taken, or -1 if max_sweeps did not converge.
-__device__ inline int jacobi_smem(double* A, double* Q, int lda, int m, JacobiScratch w, int max_sweeps) {
+// Q (same layout) receives the eigenvectors as columns: the rotations are accumulated onto the
+// identity, or onto the given Q when init_q is false (then Q^T (original) Q = A on entry, and the
+// eigenvectors of the original matrix come out).  With negl > 0 an off-diagonal element at most
+// negl (|a_pp| + |a_qq|) is set to zero instead of rotated (the classical threshold of cyclic
+// Jacobi: below the rounding of its diagonal pair it cannot change the eigenvalues).  Every thread of
+// the CTA must call it.  Returns the number of sweeps taken, or -1 if max_sweeps did not converge.
+__device__ inline int jacobi_smem(double* A, double* Q, int lda, int m, JacobiScratch w, int max_sweeps,
+                                  bool init_q = true, double negl = 0.0) {
   const int tid = threadIdx.x, nth = blockDim.x, nwarp = (nth + 31) / 32;
-  for (int idx = tid; idx < m * m; idx += nth) {
-    const int i = idx / m, j = idx % m;
-    Q[i * lda + j] = i == j ? 1.0 : 0.0;
-  }
+  if (init_q)
+    for (int idx = tid; idx < m * m; idx += nth) {
+      const int i = idx / m, j = idx % m;
+      Q[i * lda + j] = i == j ? 1.0 : 0.0;
+    }
   __syncthreads();
   const int mm = m + (m & 1), npair = mm / 2;
   for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
@@ -68,7 +74,11 @@ __device__ inline int jacobi_smem(double* A, double* Q, int lda, int m, JacobiSc
         const int b = bpos == 0 ? 0 : 1 + (bpos - 1 + r) % (mm - 1);
         const int p = min(a, b), q = max(a, b);
         double c = 1.0, s = 0.0;
-        if (q < m && A[p * lda + q] != 0.0) {
+        if (q < m && negl > 0.0 && A[p * lda + q] != 0.0 &&
+            fabs(A[p * lda + q]) <= negl * (fabs(A[p * lda + p]) + fabs(A[q * lda + q]))) {
+          A[p * lda + q] = 0.0;  // each pair is owned by one thread in this round
+          A[q * lda + p] = 0.0;
+        } else if (q < m && A[p * lda + q] != 0.0) {
           const double apq = A[p * lda + q];
           const double tau = (A[q * lda + q] - A[p * lda + p]) / (2.0 * apq);
           const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
