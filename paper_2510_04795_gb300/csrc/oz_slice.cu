@@ -148,34 +148,35 @@ __global__ void __launch_bounds__(256) digits_kernel(const SliceSeg* __restrict_
       }
       *reinterpret_cast<uint4*>(g.dst + base + (long long)t * (g.TR * KB)) = o;
     }
-    return;
-  }
-  int d[S][8];
+  } else {
+    // S = 9: the fixed-point value needs more than 64 bits
+    int d[S][8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const double v = vals[q];
-    {
-      __int128 X = fixed_point128(v, e, S);
+    for (int q = 0; q < 8; ++q) {
+      const double v = vals[q];
+      {
+        __int128 X = fixed_point128(v, e, S);
 #pragma unroll
-      for (int t = S - 1; t >= 0; --t) {
-        int dd = (int)((X + 128) & 255) - 128;
-        d[t][q] = dd;
-        X = (X - dd) >> 8;
+        for (int t = S - 1; t >= 0; --t) {
+          int dd = (int)((X + 128) & 255) - 128;
+          d[t][q] = dd;
+          X = (X - dd) >> 8;
+        }
       }
     }
-  }
 #pragma unroll
-  for (int t = 0; t < S; ++t) {
-    __half2 h0 = __halves2half2(__int2half_rn(d[t][0]), __int2half_rn(d[t][1]));
-    __half2 h1 = __halves2half2(__int2half_rn(d[t][2]), __int2half_rn(d[t][3]));
-    __half2 h2 = __halves2half2(__int2half_rn(d[t][4]), __int2half_rn(d[t][5]));
-    __half2 h3 = __halves2half2(__int2half_rn(d[t][6]), __int2half_rn(d[t][7]));
-    uint4 w;
-    w.x = *reinterpret_cast<uint32_t*>(&h0);
-    w.y = *reinterpret_cast<uint32_t*>(&h1);
-    w.z = *reinterpret_cast<uint32_t*>(&h2);
-    w.w = *reinterpret_cast<uint32_t*>(&h3);
-    *reinterpret_cast<uint4*>(g.dst + base + (long long)t * (g.TR * KB)) = w;
+    for (int t = 0; t < S; ++t) {
+      __half2 h0 = __halves2half2(__int2half_rn(d[t][0]), __int2half_rn(d[t][1]));
+      __half2 h1 = __halves2half2(__int2half_rn(d[t][2]), __int2half_rn(d[t][3]));
+      __half2 h2 = __halves2half2(__int2half_rn(d[t][4]), __int2half_rn(d[t][5]));
+      __half2 h3 = __halves2half2(__int2half_rn(d[t][6]), __int2half_rn(d[t][7]));
+      uint4 w;
+      w.x = *reinterpret_cast<uint32_t*>(&h0);
+      w.y = *reinterpret_cast<uint32_t*>(&h1);
+      w.z = *reinterpret_cast<uint32_t*>(&h2);
+      w.w = *reinterpret_cast<uint32_t*>(&h3);
+      *reinterpret_cast<uint4*>(g.dst + base + (long long)t * (g.TR * KB)) = w;
+    }
   }
 }
 
