@@ -301,7 +301,9 @@ int davidson_step(oz_davidson* d, double* theta, double* resid, int* converged, 
 int davidson_ritz(oz_davidson* d, double* d_x, oz_stream_t stream);
 /* Whole solve with max_sub = 24: d_psi is the start vector on entry and the normalised Ritz vector
  * on exit; *energy = last Ritz value, *iters = iterations.  OZ_ENOCONV when max_iter iterations did
- * not converge (d_psi and *energy then hold the last iterate). */
+ * not converge (d_psi and *energy then hold the last iterate).  The projected matrix of each
+ * iteration is the previous one bordered by one row and column, so its Jacobi solve starts from
+ * the previous eigenvectors (Davidson and Lanczos; restarts solve from scratch). */
 int davidson_solve(oz_heff* h, double* d_psi, double tol, int max_iter, double* energy, int* iters,
                    oz_stream_t stream);
 /* Lanczos alternative to davidson_solve (paper, section "Theory of TNS/DMRG ...": the Krylov
@@ -343,8 +345,9 @@ int oz_mpo_dense(const double* h1, const double* eri, int L, double* out);
  *   - U(1) x U(1) symmetry (electron number, 2 Sz); the environments are the MPO's partial sums
  *     on every block, so H_eff = sum_w L_w (x) R_w is a task list of heff_apply (emulated or
  *     native FP64 as `prec` says); its lowest eigenpair comes from davidson_solve (tolerance
- *     davidson_tol on |r|_2, at most 1000 iterations, start vector from a counter-based generator
- *     keyed by `seed` and the step number).
+ *     davidson_tol on |r|_2, at most 1000 iterations), started from the previous bond's solution
+ *     carried to this bond (oz_dmrg_set_prediction), or else from a counter-based generator keyed
+ *     by `seed` and the step number.
  *   - Start: every right block holds the single state of the reference determinant (orbitals
  *     filled from 0 with (N + 2Sz)/2 up and (N - 2Sz)/2 down electrons).
  *   - A sweep is bonds 0..L-2 left to right, then L-2..0 right to left; every bond but the last of
@@ -356,8 +359,8 @@ int oz_mpo_dense(const double* h1, const double* eri, int L, double* out);
  * more than 112 states are diagonalised in global instead of shared memory).
  * A bond whose Davidson run stops short of its tolerance keeps its best Ritz pair and is marked
  * in oz_dmrg_step.converged.  Errors: OZ_EINVAL (arguments, limits), OZ_ENOCONV (density-matrix
- * Jacobi did not converge),
- * OZ_ENONFINITE, OZ_ECUDA, OZ_ENOMEM.  Synchronous; uses its own stream on the context's device.
+ * Jacobi did not converge), OZ_ENONFINITE, OZ_ECUDA, OZ_ENOMEM.  Synchronous; uses its own stream
+ * on the context's device.
  * ------------------------------------------------------------------------------------------ */
 typedef struct oz_dmrg_s oz_dmrg;
 typedef struct oz_dmrg_step {
