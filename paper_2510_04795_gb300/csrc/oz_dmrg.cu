@@ -827,6 +827,7 @@ int predict_start(oz_dmrg* d, int i, int dir, const Bond& B, double* psi, bool* 
   if (!T || !X || !T->has_src || !X->has_src) return OZ_OK;
   const Enlarged& Bx = dir == 0 ? B.RE : B.LE;  // the new enlarged basis X's states are expanded over
   if (X->src.b.q.size() != Bx.b.q.size() || X->src.b.dim != Bx.b.dim) return OZ_OK;
+  if (T->src.b.dim != (dir == 0 ? P.LE : P.RE).b.dim) return OZ_OK;  // T was cut from the previous bond
   // new psi sector of (LE sector, RE sector)
   auto psi_sector = [&](int le, int re) {
     for (size_t p = 0; p < B.le.size(); ++p)
