@@ -26,3 +26,31 @@ def test_library_exports_every_declared_symbol():
     lib = ctypes.CDLL(_native.lib_path())
     missing = [n for n in _declared() if not hasattr(lib, n)]
     assert not missing, missing
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    # no CPU fallback: without the compiled library every entry point raises
+    import pytest
+    from paper_2510_04795_gb300 import _native
+    import paper_2510_04795_gb300 as oz
+    monkeypatch.setattr(_native, "_lib", None)
+    monkeypatch.setattr(_native, "_LIBPATH", str(tmp_path / "libozdmrg.so"))
+    with pytest.raises(_native.OzError):
+        _native.load()
+    with pytest.raises(_native.OzError):
+        oz.Context(0)
+
+
+def test_python_binding_only_marshals():
+    # the package imports no oracle module and no numerical fallback
+    import ast
+    pkg = os.path.join(ROOT, "paper_2510_04795_gb300")
+    for f in ("__init__.py", "_native.py", "selector.py"):
+        tree = ast.parse(open(os.path.join(pkg, f)).read())
+        mods = set()
+        for node in ast.walk(tree):
+            if isinstance(node, ast.Import):
+                mods.update(a.name.split(".")[0] for a in node.names)
+            elif isinstance(node, ast.ImportFrom) and node.module:
+                mods.add(node.module.split(".")[0])
+        assert "oracle" not in mods, f
