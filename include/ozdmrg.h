@@ -112,8 +112,9 @@ int oz_performant_choice(oz_ctx* ctx, int m, int n, int k, const oz_prec* prec, 
  *   - A product is rejected with OZ_EINVAL when its scratch would exceed 64 MiB (about
  *     S * 2 * (m_pad k_pad + n_pad k_pad) bytes, m padded to 128, n to 64, k to 16), when
  *     k > 1048576, or for the argument errors of ozaki_gemm.  Errors are reported by the return
- *     code only (oz_last_error is not updated) and device-side conditions (NaN/Inf inputs) are
- *     not latched: outputs are then unspecified.
+ *     code only (oz_last_error is not updated).  Device-side conditions are not reported at
+ *     all: with a NaN/Inf input, or when a kernel's bounded wait gives up (about 2 s), the call
+ *     still returns OZ_OK and C is unspecified.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) and
  *     caches it; make that first call before any stream capture.
  *   - All calls share the array and it keeps the last call's contents; the parts that must start
@@ -378,6 +379,8 @@ typedef struct oz_dmrg_step {
   double energy_fp64;  /* with the FP64 check: psi^T H_eff psi in native FP64 (else = energy) */
   int nonvariational;  /* with the FP64 check: 1 if energy < energy_fp64 - 1e-8 Eh */
   int predicted;       /* 1 if the eigensolver started from the previous bond's transformed solution */
+  int rotated;         /* 1 if the truncation chose states (density-matrix eigenvectors) and
+                          renormalised the operators; 0 if the whole enlarged block was kept */
 } oz_dmrg_step;
 int oz_dmrg_create(oz_ctx* ctx, const double* h1, const double* eri, int L, int nelec, int twosz, int D,
                    const oz_prec* prec, double davidson_tol, unsigned long long seed, oz_dmrg** out);
@@ -419,6 +422,21 @@ int oz_dmrg_set_rdm_prec(oz_dmrg* d, const oz_prec* prec);
 #define OZ_SOLVER_DAVIDSON 0
 #define OZ_SOLVER_LANCZOS 1
 int oz_dmrg_set_solver(oz_dmrg* d, int solver, double tol, int check_fp64);
+/* Verification entry points for the emulated renormalisation and density matrices (the same
+ * passages as oz_dmrg_set_renorm_prec and oz_dmrg_set_rdm_prec).  oz_dmrg_set_trace(d, stride)
+ * clears the record and, for stride > 0, copies products 0, stride, 2 stride, ... of every
+ * emulated batch that the sweep runs from then on (each truncating bond runs one batch per
+ * renormalisation pass and one of density matrices) to host memory: operands and result.
+ * stride = 0 stops recording.  The copies synchronise the sweep's stream; use it on small systems.
+ * oz_dmrg_trace(d, i, info, A, B, C, n): *n (if not null) = number of records; for i >= 0,
+ * info[0..6] = kind (0: T = O U, the first renormalisation pass of an MPO state and sector; 1:
+ * E = U^T T, the second pass; 2: a density matrix psi psi^T or psi^T psi of one sector), step
+ * (index of the oz_dmrg_steps entry of the bond), M, N, K, slices, level; A (M x K) and B (K x N)
+ * receive the operands as multiplied (op(A), op(B)) and C (M x N) the emulated result, all
+ * row-major HOST arrays that the caller sizes from info (pass null to skip).  i < 0 only sets *n.
+ * OZ_EINVAL: null handle, negative stride, i out of range. */
+int oz_dmrg_set_trace(oz_dmrg* d, int stride);
+int oz_dmrg_trace(const oz_dmrg* d, long long i, int* info, double* A, double* B, double* C, long long* n);
 /* One-shot form: create, run nsweeps, destroy. */
 int dmrg_sweep(oz_ctx* ctx, const double* h1, const double* eri, int L, int nelec, int twosz, int D, int nsweeps,
                const oz_prec* prec, double davidson_tol, unsigned long long seed, double* energies);

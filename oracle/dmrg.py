@@ -26,8 +26,11 @@ Conventions (readings where the paper is silent):
    the squared singular values), keep the largest ones above 1e-14, at most D of them, and never
    cut through a group of equal eigenvalues (those within 1e-12 lambda_max + 1e-8 lambda at the
    cut, e.g. members of a spin multiplet): the whole group is dropped instead.
+ * Emulated density matrices (the paper's truncation-precision study, same section): with
+   ``rdm = (S, s)`` every rho is the emulated product of ``ozaki.ozaki_gemm`` instead of FP64.
 Parity: pinned (tests/test_oracle_dmrg.py) by FCI: without truncation the sweep energy equals
-the FCI energy, with truncation it stays above it and decreases sweep by sweep.
+the FCI energy, with truncation it stays above it and decreases sweep by sweep; with emulated
+density matrices at S = 7 (noise far below the keep threshold) the sweep is the FP64 one.
 """
 from __future__ import annotations
 
@@ -35,7 +38,7 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from . import fci
+from . import fci, ozaki
 
 SITE_Q = [(0, 0), (1, 1), (1, -1), (2, 0)]   # (electrons, 2 Sz) of the site states 0..3
 LAMBDA_MIN = 1e-14
@@ -120,9 +123,11 @@ def select_kept(lams: list, D: int) -> int:
     return k
 
 
-def _truncate(enl: dict, psi_blocks: dict, D: int, left: bool) -> dict:
+def _truncate(enl: dict, psi_blocks: dict, D: int, left: bool, rdm=None) -> dict:
     """New block from the enlarged block ``enl`` and the two-site blocks psi_blocks[q] (rows: the
-    enlarged sector q of the left side; columns: the right side), by the rule of the header."""
+    enlarged sector q of the left side; columns: the right side), by the rule of the header.
+    ``rdm = (S, s)`` forms every density matrix as the emulated product of ``ozaki.ozaki_gemm``
+    (S slices used at level s) instead of in FP64; the eigendecomposition stays FP64."""
     total = sum(sec.k for sec in enl.values())
     if total <= D:
         return enl
@@ -132,7 +137,10 @@ def _truncate(enl: dict, psi_blocks: dict, D: int, left: bool) -> dict:
         M = psi_blocks.get(q)
         if M is None or M.size == 0:
             continue
-        rho = M @ M.T if left else M.T @ M
+        if rdm is None:
+            rho = M @ M.T if left else M.T @ M
+        else:
+            rho = ozaki.ozaki_gemm(M, M.T, rdm[0], rdm[1]) if left else ozaki.ozaki_gemm(M.T, M, rdm[0], rdm[1])
         w, V = np.linalg.eigh(0.5 * (rho + rho.T))
         w, V = w[::-1], V[:, ::-1]
         eig[q] = (w, V)
@@ -175,7 +183,7 @@ def _reference_blocks(L, nelec, twosz):
 class ExplicitDMRG:
     """Two-site DMRG with explicit block bases (see the module header)."""
 
-    def __init__(self, h, eri, nelec: int, twosz: int, D: int, eig_tol: float = 1e-13):
+    def __init__(self, h, eri, nelec: int, twosz: int, D: int, eig_tol: float = 1e-13, rdm=None):
         self.L = h.shape[0]
         self.N, self.twosz, self.D = nelec, twosz, D
         self.H, pats = orbital_major_hamiltonian(h, eri, nelec, twosz)
@@ -183,6 +191,7 @@ class ExplicitDMRG:
         self.index[pats] = np.arange(len(pats))
         self.target = (nelec, twosz)
         self.eig_tol = eig_tol
+        self.rdm = rdm          # None (FP64 density matrices) or (S, s) for emulated ones
         vac = {(0, 0): _Sector((0, 0), [0], np.ones((1, 1)))}
         self.left = {0: vac}                       # left[i]: block of orbitals 0..i-1
         self.right = _reference_blocks(self.L, nelec, twosz)   # right[j]: orbitals j..L-1
@@ -223,11 +232,11 @@ class ExplicitDMRG:
                 E, blocks, LE, RE, _ = self._solve(i)
                 self.energies.append(E)
                 if i < L - 2:
-                    self.left[i + 1] = _truncate(LE, blocks, self.D, left=True)
+                    self.left[i + 1] = _truncate(LE, blocks, self.D, left=True, rdm=self.rdm)
             for i in range(L - 2, -1, -1):
                 E, blocks, LE, RE, _ = self._solve(i)
                 self.energies.append(E)
                 if i > 0:
                     rblocks = {(self.target[0] - q[0], self.target[1] - q[1]): M for q, M in blocks.items()}
-                    self.right[i + 1] = _truncate(RE, rblocks, self.D, left=False)
+                    self.right[i + 1] = _truncate(RE, rblocks, self.D, left=False, rdm=self.rdm)
         return self.energies

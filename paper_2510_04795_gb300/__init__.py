@@ -407,6 +407,27 @@ class DMRG:
         N.check(self.lib.oz_dmrg_steps(self.h, arr, n.value, C.byref(n)))
         return [{f: getattr(arr[i], f) for f, _ in N.oz_dmrg_step._fields_} for i in range(n.value)]
 
+    def set_trace(self, stride: int):
+        """Record every stride-th emulated renormalisation / density-matrix product from now on
+        (0 = off; clears the record)."""
+        N.check(self.lib.oz_dmrg_set_trace(self.h, int(stride)))
+
+    def trace(self) -> list:
+        """The recorded products: dicts with kind (0: T = O U, 1: U^T T, 2: density matrix), step,
+        slices, level and the host arrays A (op(A)), B (op(B)) and C (the emulated result)."""
+        import numpy as np
+        n = C.c_longlong()
+        N.check(self.lib.oz_dmrg_trace(self.h, -1, None, None, None, None, C.byref(n)))
+        out = []
+        info = (C.c_int * 7)()
+        for i in range(n.value):
+            N.check(self.lib.oz_dmrg_trace(self.h, i, info, None, None, None, None))
+            kind, step, m, nn, k, S, lv = list(info)
+            A, B, Cm = np.empty((m, k)), np.empty((k, nn)), np.empty((m, nn))
+            N.check(self.lib.oz_dmrg_trace(self.h, i, None, A.ctypes.data, B.ctypes.data, Cm.ctypes.data, None))
+            out.append({"kind": kind, "step": step, "slices": S, "level": lv, "A": A, "B": B, "C": Cm})
+        return out
+
     def bond_heff(self, bond: int, psi: torch.Tensor | None = None, stream=None):
         """(H_eff psi or None, determinant pattern of every two-site basis state) at a bond."""
         import numpy as np

@@ -42,7 +42,8 @@ class oz_dmrg_step(C.Structure):
     _fields_ = [("sweep", C.c_int), ("dir", C.c_int), ("bond", C.c_int), ("dim", C.c_int), ("nterm", C.c_int),
                 ("ntask", C.c_int), ("iters", C.c_int), ("converged", C.c_int), ("kept", C.c_int),
                 ("energy", C.c_double), ("discarded", C.c_double), ("energy_fp64", C.c_double),
-                ("nonvariational", C.c_int), ("predicted", C.c_int)]
+                ("nonvariational", C.c_int), ("predicted", C.c_int),
+                ("rotated", C.c_int)]
 
 
 _lib = None
@@ -115,6 +116,8 @@ def load():
         "oz_dmrg_set_prediction": (i, [vp, i]),
         "oz_dmrg_steps": (i, [vp, vp, i, C.POINTER(i)]),
         "oz_dmrg_bond_heff": (i, [vp, i, vp, vp, vp, C.POINTER(ll), vp]),
+        "oz_dmrg_set_trace": (i, [vp, i]),
+        "oz_dmrg_trace": (i, [vp, ll, vp, vp, vp, vp, C.POINTER(ll)]),
         "dmrg_sweep": (i, [vp, vp, vp, i, i, i, i, i, C.POINTER(oz_prec), d, C.c_ulonglong, vp]),
     }
     for name, (res, args) in sig.items():

@@ -375,10 +375,62 @@ struct oz_dmrg_s {
     Enlarged LE, RE;
   } prev;
   DevBuf prev_psi, pred_tmp, pred_jobs;
+  // verification record of emulated renormalisation and density-matrix products (oz_dmrg_set_trace)
+  struct TraceRec {
+    int kind, step, M, N, K, S, level;
+    std::vector<double> A, B, C;  // op(A) M x K, op(B) K x N, C M x N, row-major
+  };
+  int trace_stride = 0;
+  std::vector<TraceRec> trace;
   QN target() const { return {N, twosz}; }
 };
 
 namespace {
+
+// Host copy of rows x cols of a row-major device matrix (leading dimension ld), transposed into
+// cols x rows when `trans` is set.
+int fetch_matrix(const double* src, long long ld, int rows, int cols, bool trans, std::vector<double>* out,
+                 cudaStream_t st) {
+  std::vector<double> tmp((size_t)rows * cols);
+  DM_CU(cudaMemcpy2DAsync(tmp.data(), (size_t)cols * 8, src, (size_t)ld * 8, (size_t)cols * 8, rows,
+                          cudaMemcpyDeviceToHost, st));
+  DM_CU(cudaStreamSynchronize(st));
+  if (!trans) {
+    out->swap(tmp);
+    return OZ_OK;
+  }
+  out->assign((size_t)rows * cols, 0.0);
+  for (int r = 0; r < rows; ++r)
+    for (int c = 0; c < cols; ++c) (*out)[(size_t)c * rows + r] = tmp[(size_t)r * cols + c];
+  return OZ_OK;
+}
+
+// Records products 0, stride, 2 stride, ... of an emulated batch that has completed on d->st (so
+// every batch, i.e. every truncating bond, leaves at least one record): kind 0 = renormalisation
+// T = O U, 1 = renormalisation U^T T, 2 = density matrix.
+int trace_batch(oz_dmrg* d, int kind, const std::vector<oz::EmuJob>& jobs, int S, int lv) {
+  if (d->trace_stride <= 0) return OZ_OK;
+  for (size_t idx = 0; idx < jobs.size(); idx += (size_t)d->trace_stride) {
+    const oz::EmuJob& j = jobs[idx];
+    oz_dmrg_s::TraceRec r;
+    r.kind = kind;
+    r.step = (int)d->steps.size();
+    r.M = j.M;
+    r.N = j.N;
+    r.K = j.K;
+    r.S = S;
+    r.level = lv;
+    // op(A) = A (M x K) or the transpose of the stored K x M matrix
+    DM_RC(j.transA ? fetch_matrix(j.A, j.lda, j.K, j.M, true, &r.A, d->st)
+                   : fetch_matrix(j.A, j.lda, j.M, j.K, false, &r.A, d->st));
+    // op(B) = B (K x N) or the transpose of the stored N x K matrix
+    DM_RC(j.transB ? fetch_matrix(j.B, j.ldb, j.N, j.K, true, &r.B, d->st)
+                   : fetch_matrix(j.B, j.ldb, j.K, j.N, false, &r.B, d->st));
+    DM_RC(fetch_matrix(j.C, j.ldc, j.M, j.N, false, &r.C, d->st));
+    d->trace.push_back(std::move(r));
+  }
+  return OZ_OK;
+}
 
 // Operators of the enlarged block: L_w (left) for the states of bond `site`, or R_w (right) for
 // the states of bond `site` - 1.
@@ -544,7 +596,9 @@ int project(oz_dmrg* d, const Enlarged& X, Ops& ops, bool keep_all, const std::v
     for (const GemmJob& g : g2) e2.push_back({g.A, g.lda, 1, g.B, g.ldb, 0, g.C, g.ldc, g.M, g.N, g.K});
     const int S = d->renorm.slices, lv = d->renorm.level ? d->renorm.level : d->renorm.slices;
     DM_RC(oz::emulated_batch(d->ctx, e1, S, lv, d->st));
+    DM_RC(trace_batch(d, 0, e1, S, lv));
     DM_RC(oz::emulated_batch(d->ctx, e2, S, lv, d->st));
+    DM_RC(trace_batch(d, 1, e2, S, lv));
   } else if (!g1.empty()) {
     DM_RC(d->jobs.upload(g1, d->st));
     small_gemm_kernel<<<(unsigned)g1.size(), 128, 0, d->st>>>((const GemmJob*)d->jobs.p);
@@ -679,6 +733,7 @@ int choose_states(oz_dmrg* d, Bond& B, const double* psi, bool left, bool* keep_
       ejb.push_back({g.A, g.lda, g.ta, g.B, g.ldb, g.tb, g.C, g.ldc, g.M, g.N, g.K});
     const int lv = d->rdm.level ? d->rdm.level : d->rdm.slices;
     DM_RC(oz::emulated_batch(d->ctx, ejb, d->rdm.slices, lv, d->st));
+    DM_RC(trace_batch(d, 2, ejb, d->rdm.slices, lv));
   } else {
     DM_RC(d->jobs.upload(gj, d->st));
     small_gemm_kernel<<<(unsigned)gj.size(), 128, 0, d->st>>>((const GemmJob*)d->jobs.p);
@@ -1036,6 +1091,7 @@ int solve_bond(oz_dmrg* d, int i, int dir, int sweep, bool truncate) {
     auto Env_ = std::make_unique<Env>();
     DM_RC(project(d, left ? B.LE : B.RE, left ? B.Lw : B.Rw, keep_all, U, k, pats, Env_.get()));
     s.kept = (int)Env_->basis.total();
+    s.rotated = keep_all ? 0 : 1;
     s.discarded = disc;
     if (left) d->left[i + 1] = std::move(Env_);
     else d->right[i] = std::move(Env_);
@@ -1185,4 +1241,29 @@ extern "C" int dmrg_sweep(oz_ctx* ctx, const double* h1, const double* eri, int 
   const int rc = oz_dmrg_run(d, nsweeps, energies);
   oz_dmrg_destroy(d);
   return rc;
+}
+
+extern "C" int oz_dmrg_set_trace(oz_dmrg* d, int stride) {
+  if (!d) return oz::api_fail(OZ_EINVAL, "null handle");
+  if (stride < 0) return oz::api_fail(OZ_EINVAL, "stride must be >= 0");
+  d->trace_stride = stride;
+  d->trace.clear();
+  return OZ_OK;
+}
+
+extern "C" int oz_dmrg_trace(const oz_dmrg* d, long long i, int* info, double* A, double* B, double* C,
+                             long long* n) {
+  if (!d) return oz::api_fail(OZ_EINVAL, "null handle");
+  if (n) *n = (long long)d->trace.size();
+  if (i < 0) return OZ_OK;
+  if (i >= (long long)d->trace.size()) return oz::api_fail(OZ_EINVAL, "trace record index out of range");
+  const oz_dmrg_s::TraceRec& r = d->trace[(size_t)i];
+  if (info) {
+    const int v[7] = {r.kind, r.step, r.M, r.N, r.K, r.S, r.level};
+    std::memcpy(info, v, sizeof(v));
+  }
+  if (A) std::memcpy(A, r.A.data(), r.A.size() * 8);
+  if (B) std::memcpy(B, r.B.data(), r.B.size() * 8);
+  if (C) std::memcpy(C, r.C.data(), r.C.size() * 8);
+  return OZ_OK;
 }

@@ -27,6 +27,7 @@
 #include "oz_gemm.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <utility>
 #include <vector>
 
@@ -514,11 +515,18 @@ void balance_tiles(const std::vector<GemmProblem>& probs, std::vector<GemmTile>&
 cudaError_t launch_gemm(const GemmProblem* d_probs, const GemmTile* d_tiles, int ntiles, int grid,
                         const GemmProblem* single, int smax, int* d_err, cudaStream_t st, const int* d_first) {
   if (ntiles <= 0) return cudaSuccess;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
+  // The shared-memory opt-in belongs to the current device's context: record it per device
+  // ordinal (bit d of a process-wide mask).  Setting it twice is harmless, so two host threads
+  // racing on the same device need no lock.
+  static std::atomic<unsigned long long> attr_set{0ull};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (!bit || !(attr_set.load(std::memory_order_acquire) & bit)) {
+    e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
     if (e != cudaSuccess) return e;
-    attr = true;
+    attr_set.fetch_or(bit, std::memory_order_release);
   }
   GemmProblem one{};
   if (single) {

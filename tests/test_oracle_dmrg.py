@@ -60,3 +60,18 @@ def test_dmrg_c0_d64_against_fci():
     assert np.all(E >= e0 - 1e-10)
     assert abs(E[1, 0, 3] - e0) < 1e-10
     assert 0 < E[1, 1, -1] - e0 < 1e-2
+
+
+def test_dmrg_emulated_density_matrices_at_seven_slices_is_fp64():
+    # seven slices carry 55 bits: the emulated rho differs from the FP64 one by about 2^-56 of its
+    # norm, far below the keep threshold, so the truncations and energies are those of FP64;
+    # two slices (15 bits) move the energies visibly but keep them above FCI
+    L, N = 6, 6
+    h, eri = synthetic.integrals(L, seed=0)
+    e0 = fci.ground_state(h, eri, N, 0)[0]
+    ref = np.array(dmrg.ExplicitDMRG(h, eri, N, 0, D=8).sweep(2))
+    e7 = np.array(dmrg.ExplicitDMRG(h, eri, N, 0, D=8, rdm=(7, 7)).sweep(2))
+    assert np.max(np.abs(e7 - ref)) < 1e-10
+    e2 = np.array(dmrg.ExplicitDMRG(h, eri, N, 0, D=8, rdm=(2, 2)).sweep(2))
+    assert np.all(e2 >= e0 - 1e-10)
+    assert np.max(np.abs(e2 - ref)) > 1e-9
