@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-validate", action="store_true", help="skip the |dE| check of the two-site sweep")
     p.add_argument("--no-autotune", action="store_true", help="keep the default tile schedule")
+    p.add_argument("--no-sweep", action="store_true", help="skip the slice-count sweep on the 40-block workload")
     p.add_argument("--no-select", action="store_true",
                    help="skip the informational per-block-level run (analytic selector, 1e-12 budget)")
     return p.parse_args()
@@ -273,6 +274,47 @@ def validation_sweep(ctx, slices: int):
             "sweep_s_gpu": t_gpu, "sweep_s_oracle_cpu": t_or}
 
 
+def slice_sweep(ctx):
+    """The precision dial on the 40-block workload (sizes 8-256, entries N(0,1) 2^-j with j up to 19:
+    about six decades of exponent spread inside every block, 128 terms): H_eff psi with s slices for
+    s = 3..8 (an S = 9 handle multiplies at level 8, so s = 9 is not a separate row), its relative
+    Frobenius error against the FP64 oracle (per-block numpy products on the host) and its throughput."""
+    import numpy as np
+    import torch
+    import synthetic
+    import paper_2510_04795_gb300 as oz
+    from oracle import heff as OH
+    st = synthetic.heff_structure(**synthetic.CONFIGS["heff40_8-256"])
+    F = st.flops()
+    blocks = [synthetic.gen_task_blocks(st, t) for t in range(st.ntask)]
+    psi_h = synthetic.gen_psi(st)
+    ref = OH.heff_apply_fp64(st, [b[0].numpy() for b in blocks], [b[1].numpy() for b in blocks], psi_h.numpy())
+    tasks = [(int(sr), int(d), float(st.term_coef[k]), L.cuda(), R.cuda())
+             for (k, sr, d), (L, R) in zip(st.tasks, blocks)]
+    psi = psi_h.cuda()
+    rows = []
+    for s in range(3, 9):
+        h = oz.Heff(ctx, st.m, st.n, tasks, slices=s)
+        y = h.apply(psi)
+        for _ in range(3):
+            h.apply(psi, y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(10):
+            h.apply(psi, y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        yh = y.cpu().numpy()
+        rows.append({"s": s, "rel_frobenius_vs_fp64_oracle": float(np.linalg.norm(yh - ref) / np.linalg.norm(ref)),
+                     "ms_per_step": ms, "value": F / (ms * 1e-3) / 1e12, "unit": UNIT})
+        h.close()
+    ctx.status()
+    return {"workload": "heff40_8-256: 40 sector blocks 8-256, 128 terms, six-decade exponent spread per entry",
+            "tasks": st.ntask, "fp64_flop_per_step": F, "rows": rows}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -327,6 +369,7 @@ def main():
         torch.cuda.empty_cache()
 
     h = oz.Heff(ctx, st.m, st.n, tasks, slices=S)
+    ops_ms, ops_bytes = oz.heff_ops_times(h)
     del tasks, Lbuf, Rbuf
     torch.cuda.empty_cache()
     tuned = None
@@ -426,6 +469,18 @@ def main():
            "peak": hbm_peak, "unit": "GB/s", "frac": hbm_ach / hbm_peak, "bytes_read": rd, "bytes_written": wr,
            "peak_source": f"hbm_gbs ({pk_src})"}
 
+    ops_slicing = {"kernels": "oz::rowmax_kernel + oz::digits_kernel<%d> over every operator block (once per "
+                              "operator set: oz_heff_create / oz_heff_update_ops)" % S,
+                   "rowmax_ms": ops_ms[0], "digits_ms": ops_ms[1], "bytes": ops_bytes,
+                   "achieved": sum(ops_bytes) / (sum(ops_ms) * 1e-3) / 1e9 if sum(ops_ms) > 0 else None,
+                   "peak": hbm_peak, "unit": "GB/s"}
+    if ops_slicing["achieved"]:
+        ops_slicing["frac"] = ops_slicing["achieved"] / hbm_peak
+
+    sweep = None
+    if rank == 0 and not args.no_sweep:
+        sweep = slice_sweep(ctx)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         from oracle import heff as OH
@@ -483,6 +538,8 @@ def main():
         "davidson": dav,
         "autotune": tuned,
         "per_block_levels": select,
+        "operator_slicing": ops_slicing,
+        "slice_sweep": sweep,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -186,6 +186,12 @@ int heff_apply_host(oz_heff* h, const double* psi_host, double* y_host, oz_strea
  * from CUDA events recorded on its stream: [0] slicing of psi, [1] stage-1 GEMM launch,
  * [2] slicing of the intermediate, [3] stage-2 GEMM launch.  Waits for that product to finish. */
 int oz_heff_stage_times(oz_heff* h, float* ms4);
+/* Device ms (ms2[0] rowmax pass, ms2[1] digit pass; CUDA events) and algorithmic bytes of the last
+ * operator slicing of an emulated handle (oz_heff_create or oz_heff_update_ops): bytes2[0] = 8 per
+ * operator element read by the row-maximum pass; bytes2[1] = 8 per element read plus 2S per
+ * element of the 8 x 8-padded digit tiles written.  Zeros for a native handle.  Either pointer may
+ * be null. */
+int oz_heff_ops_times(const oz_heff* h, float* ms2, long long* bytes2);
 /* Sizes and bookkeeping of the handle. */
 typedef struct oz_heff_info {
   long long dim;          /* length of psi */
@@ -213,6 +219,29 @@ int oz_heff_get_levels(const oz_heff* h, int* s1, int* s2);
  * choice for stage 1 and 2; ms (6 floats, may be null) the best stage-1 / stage-2 time of each
  * schedule.  Synchronous.  Results do not depend on the schedule. */
 int oz_heff_autotune(oz_heff* h, const double* d_psi, int reps, int* sched, float* ms, oz_stream_t stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Term sharding over several GPUs (paper, section "Numerical procedure" and the timing discussion:
+ * the sweeps run on one multi-GPU node; how the effective-Hamiltonian work is divided is not
+ * described, so the natural split of the task sum is used).  Each rank builds an H_eff handle from
+ * the tasks it owns (oz_heff_create with that subset), computes its partial Y with heff_apply,
+ * exchanges the partial vectors (a collective of the caller's framework) and sums them with
+ * oz_reduce_ordered.  The stage-2 exponents are shared by the tasks of a target sector on one
+ * handle, so the sharded sum equals the single-handle product within the emulation's accuracy,
+ * not bit for bit.
+ * oz_heff_partition: HOST function (no GPU needed).  owner[t] in 0..world-1 for every task t of
+ *   the structure (m[nsec], n[nsec], src[ntask], dst[ntask]): tasks in descending order of FP64
+ *   flop cost 2 m[dst] m[src] n[src] + 2 m[dst] n[src] n[dst] (equal costs in task order), each
+ *   onto the rank with the least cost so far (ties to the lower rank).  Deterministic: every rank
+ *   computes the same table.  OZ_EINVAL: world < 1, sector out of range, null pointers.
+ * oz_reduce_ordered: d_out[i] = ((p_0[i] + p_1[i]) + p_2[i]) + ... in FP64 on `stream`, one
+ *   rounding per addition in part order (a result independent of arrival order).  d_parts is a
+ *   HOST array of nparts (1..64) DEVICE pointers of length len; d_out may alias d_parts[0].
+ *   OZ_EINVAL on bad arguments, OZ_ECUDA on a launch failure.
+ * ------------------------------------------------------------------------------------------ */
+int oz_heff_partition(int nsec, const int* m, const int* n, int ntask, const int* src, const int* dst, int world,
+                      int* owner);
+int oz_reduce_ordered(const double* const* d_parts, int nparts, long long len, double* d_out, oz_stream_t stream);
 
 /* ------------------------------------------------------------------------------------------
  * Slice-level selection per block (the precision dial of sections "Theory of emulated FP64

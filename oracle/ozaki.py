@@ -59,6 +59,34 @@ def fixed_point(A: np.ndarray, e: np.ndarray, S: int) -> np.ndarray:
     return X
 
 
+def fixed_point_int(A: np.ndarray, e: np.ndarray, S: int) -> np.ndarray:
+    """The same X_ij = RN_even(a_ij * 2^(8S-1-e_i)) as ``fixed_point``, as int64, for S <= 7
+    (|X| < 2^55): a_ij = +-m 2^E with m the integer significand, so X = RN_even(m 2^(E+8S-1-e_i)),
+    a left shift or a right shift rounded half to even, done on the integer m.  Equality with the
+    Fraction definition is pinned in tests/test_oracle_ozaki.py."""
+    if S > 7:
+        raise ValueError("fixed_point_int needs S <= 7")
+    A = np.asarray(A, dtype=np.float64)
+    bits = A.view(np.int64)
+    be = (bits >> 52) & 0x7FF
+    f = bits & ((1 << 52) - 1)
+    m = np.where(be > 0, f | (1 << 52), f)
+    E = np.where(be > 0, be - 1075, -1074)
+    sh = E + (8 * S - 1) - np.asarray(e, dtype=np.int64).reshape(-1, 1)
+    X = np.zeros(A.shape, dtype=np.int64)
+    left = sh >= 0
+    X[left] = m[left] << sh[left]
+    right = (~left) & (sh > -64)
+    r = -sh[right]
+    mr = m[right]
+    q = mr >> r
+    rem = mr - (q << r)
+    half = np.int64(1) << (r - 1)
+    q = q + ((rem > half) | ((rem == half) & ((q & 1) == 1))).astype(np.int64)
+    X[right] = q
+    return np.where(bits < 0, -X, X)
+
+
 def digits(X: np.ndarray, S: int) -> list:
     """Balanced base-256 digits of every entry: list of S int64 arrays, d_1 first."""
     D = [np.zeros(X.shape, dtype=np.int64) for _ in range(S)]
@@ -75,10 +103,26 @@ def digits(X: np.ndarray, S: int) -> list:
     return D
 
 
+def digits_int(X: np.ndarray, S: int) -> list:
+    """``digits`` for an int64 array X (|X| < 2^55): the same balanced base-256 digits."""
+    x = np.asarray(X, dtype=np.int64).copy()
+    D = [None] * S
+    for t in range(S - 1, -1, -1):
+        d = ((x + 128) % 256) - 128
+        D[t] = d
+        x = (x - d) >> 8
+    if np.any(x != 0):
+        raise ValueError("fixed-point value outside the S-digit balanced range")
+    return D
+
+
 def slice_rows(A: np.ndarray, S: int):
-    """Per-row exponents and S digit planes of A (A-role operand)."""
+    """Per-row exponents and S digit planes of A (A-role operand).  S <= 7 takes the integer form
+    of the fixed point and digits (``fixed_point_int``, ``digits_int``), S >= 8 the Fraction form."""
     A = np.asarray(A, dtype=np.float64)
     e = row_exponents(A)
+    if S <= 7:
+        return e, digits_int(fixed_point_int(A, e, S), S)
     return e, digits(fixed_point(A, e, S), S)
 
 

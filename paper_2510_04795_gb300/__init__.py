@@ -18,8 +18,9 @@ from ._native import OzError, OZ_MODE_EAGER, OZ_MODE_NATIVE, OZ_NFEAT
 SELECTORS = {"fixed": N.OZ_SELECT_FIXED, "analytic": N.OZ_SELECT_ANALYTIC, "learned": N.OZ_SELECT_LEARNED}
 
 __all__ = ["Context", "Heff", "Davidson", "OzError", "ozaki_gemm", "performant_choice", "ozaki_slice", "ozaki_slice_products",
-           "heff_apply", "heff_apply_host", "heff_stage_times", "davidson_solve", "symeig_small", "DMRG",
-           "dmrg_sweep", "MLP", "OZ_NFEAT", "SELECTORS", "lanczos_solve",
+           "heff_apply", "heff_apply_host", "heff_stage_times", "heff_ops_times", "davidson_solve", "symeig_small", "DMRG",
+           "dmrg_sweep", "MLP", "OZ_NFEAT", "SELECTORS", "lanczos_solve", "heff_partition", "reduce_ordered",
+           "ShardedHeff",
            "OZ_MODE_EAGER", "OZ_MODE_NATIVE"]
 
 
@@ -289,6 +290,70 @@ def heff_apply_host(h: Heff, psi_host: torch.Tensor, y_host: torch.Tensor, strea
         raise OzError(N.OZ_EINVAL, "expected host float64 tensors")
     N.check(h.lib.heff_apply_host(h.h, psi_host.data_ptr(), y_host.data_ptr(), _stream(stream)))
     return y_host
+
+
+def heff_partition(m, n, src, dst, world: int):
+    """Owner rank of every task (host computation, no GPU): a balanced, deterministic split of the
+    task list over ``world`` ranks by FP64 flop cost (``oz_heff_partition``)."""
+    import numpy as np
+    lib = N.load()
+    m = np.ascontiguousarray(m, dtype=np.int32)
+    n = np.ascontiguousarray(n, dtype=np.int32)
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    owner = np.zeros(len(src), dtype=np.int32)
+    N.check(lib.oz_heff_partition(len(m), m.ctypes.data, n.ctypes.data, len(src), src.ctypes.data,
+                                  dst.ctypes.data, int(world), owner.ctypes.data))
+    return owner
+
+
+def reduce_ordered(parts, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """out = ((parts[0] + parts[1]) + parts[2]) + ... elementwise in FP64 (CUDA tensors, one
+    rounding per addition in list order)."""
+    _check_f64(*parts)
+    if out is None:
+        out = torch.empty_like(parts[0])
+    arr = (C.c_void_p * len(parts))(*[p.data_ptr() for p in parts])
+    N.check(N.load().oz_reduce_ordered(arr, len(parts), parts[0].numel(), _ptr(out), _stream(stream)))
+    return out
+
+
+class ShardedHeff:
+    """This rank's share of a term-sharded H_eff: a handle built from the tasks that
+    ``heff_partition`` gives to ``rank``; ``apply`` computes the partial product, gathers the
+    partial vectors of all ranks over ``torch.distributed`` (``group``) and sums them in rank
+    order with ``reduce_ordered``.  With world = 1 it is the unsharded product."""
+
+    def __init__(self, ctx: Context, m, n, tasks, rank: int, world: int, group=None, slices=7, level=0,
+                 mode="eager"):
+        owner = heff_partition(m, n, [t[0] for t in tasks], [t[1] for t in tasks], world)
+        self.rank, self.world, self.group = int(rank), int(world), group
+        self.owned = [i for i, o in enumerate(owner) if o == rank]
+        self.local = Heff(ctx, m, n, [tasks[i] for i in self.owned], slices=slices, level=level, mode=mode)
+        self.dim = self.local.dim
+
+    def apply_partial(self, psi: torch.Tensor, y: torch.Tensor | None = None) -> torch.Tensor:
+        return self.local.apply(psi, y)
+
+    def apply(self, psi: torch.Tensor) -> torch.Tensor:
+        part = self.local.apply(psi)
+        if self.world == 1:
+            return part
+        import torch.distributed as dist
+        parts = [torch.empty_like(part) for _ in range(self.world)]
+        dist.all_gather(parts, part, group=self.group)
+        return reduce_ordered(parts)
+
+    def close(self):
+        self.local.close()
+
+
+def heff_ops_times(h: Heff):
+    """([rowmax ms, digits ms], [rowmax bytes, digits bytes]) of the handle's last operator slicing."""
+    ms = (C.c_float * 2)()
+    by = (C.c_longlong * 2)()
+    N.check(h.lib.oz_heff_ops_times(h.h, ms, by))
+    return [float(x) for x in ms], [int(x) for x in by]
 
 
 def heff_stage_times(h: Heff) -> list:

@@ -117,6 +117,9 @@ def load():
         "oz_dmrg_steps": (i, [vp, vp, i, C.POINTER(i)]),
         "oz_dmrg_bond_heff": (i, [vp, i, vp, vp, vp, C.POINTER(ll), vp]),
         "oz_dmrg_set_trace": (i, [vp, i]),
+        "oz_heff_partition": (i, [i, vp, vp, i, vp, vp, i, vp]),
+        "oz_heff_ops_times": (i, [vp, vp, vp]),
+        "oz_reduce_ordered": (i, [vp, i, ll, vp, vp]),
         "oz_dmrg_trace": (i, [vp, ll, vp, vp, vp, vp, C.POINTER(ll)]),
         "dmrg_sweep": (i, [vp, vp, vp, i, i, i, i, i, C.POINTER(oz_prec), d, C.c_ulonglong, vp]),
     }

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 OBJ_DIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(OUT_DIR, "libozdmrg.so")
-SOURCES = ["oz_slice.cu", "oz_gemm.cu", "oz_api.cu", "oz_noalloc.cu", "oz_davidson.cu", "oz_mpo.cu", "oz_dmrg.cu", "oz_mlp.cu", "oz_select.cu"]
+SOURCES = ["oz_slice.cu", "oz_gemm.cu", "oz_api.cu", "oz_noalloc.cu", "oz_davidson.cu", "oz_mpo.cu", "oz_dmrg.cu", "oz_mlp.cu", "oz_select.cu", "oz_shard.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

@@ -167,9 +167,9 @@ int slice_pair(oz_ctx* c, int m, int n, int k, const double* A, int lda, const d
   b.r0 = 0; b.k0 = 0; b.trans = 1; b.S = S; b.scale = 1.0; b.dst = o.dB; b.TR = oz::BN; b.nkb = o.nkb;
   b.rowmax = o.mx + o.mpad; b.rowexp = o.ex + o.mpad;
   b.unit0 = oz::digit_units(a.prows, a.pcols);
-  b.unit0m = oz::rowmax_units(a.rows, a.cols);
+  b.unit0m = oz::rowmax_units(a.rows, a.cols, a.trans);
   const int nseg = B ? 2 : 1;
-  long long um = b.unit0m + (B ? oz::rowmax_units(b.rows, b.cols) : 0);
+  long long um = b.unit0m + (B ? oz::rowmax_units(b.rows, b.cols, b.trans) : 0);
   long long ud = b.unit0 + (B ? oz::digit_units(b.prows, b.pcols) : 0);
   OZ_CU(oz::launch_rowmax(nullptr, &pk, nseg, um, c->d_flags, st));
   OZ_CU(oz::launch_digits(nullptr, &pk, nseg, ud, S, st));
@@ -453,7 +453,7 @@ int slice_ops(oz_heff_s* h, const oz_task* tasks) {
       g.rowmax = h->mA1 + h->A1row[q]; g.rowexp = h->eA1 + h->A1row[q];
       g.unit0 = ud; g.unit0m = um;
       ud += oz::digit_units(g.prows, g.pcols);
-      um += oz::rowmax_units(g.rows, g.cols);
+      um += oz::rowmax_units(g.rows, g.cols, g.trans);
       ops.push_back(g);
     }
   for (int q = 0; q < h->nsec; ++q)
@@ -466,7 +466,7 @@ int slice_ops(oz_heff_s* h, const oz_task* tasks) {
       g.rowmax = h->mB2 + h->B2row[q]; g.rowexp = h->eB2 + h->B2row[q];
       g.unit0 = ud; g.unit0m = um;
       ud += oz::digit_units(g.prows, g.pcols);
-      um += oz::rowmax_units(g.rows, g.cols);
+      um += oz::rowmax_units(g.rows, g.cols, g.trans);
       ops.push_back(g);
     }
   if (ops.empty()) return OZ_OK;
@@ -476,10 +476,34 @@ int slice_ops(oz_heff_s* h, const oz_task* tasks) {
   SliceSeg* dops;
   OZ_CU(cudaMalloc(&dops, ops.size() * sizeof(SliceSeg)));
   cudaMemcpy(dops, ops.data(), ops.size() * sizeof(SliceSeg), cudaMemcpyHostToDevice);
+  // algorithmic bytes: the rowmax pass reads every operator element once; the digit pass reads it
+  // again and writes S FP16 digits per element of the 8 x 8-padded segment
+  long long brm = 0, bdg = 0;
+  for (const SliceSeg& g : ops) {
+    brm += 8ll * g.rows * g.cols;
+    bdg += 8ll * g.rows * g.cols + 2ll * S * ((g.prows + 7) / 8 * 8) * ((g.pcols + 7) / 8 * 8);
+  }
+  cudaEvent_t t0 = nullptr, t1 = nullptr, t2 = nullptr;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  cudaEventCreate(&t2);
+  cudaEventRecord(t0, 0);
   cudaError_t e1 = oz::launch_rowmax(dops, nullptr, (int)ops.size(), um, c->d_flags, 0);
+  cudaEventRecord(t1, 0);
   cudaError_t e2 = oz::launch_digits(dops, nullptr, (int)ops.size(), ud, S, 0);
+  cudaEventRecord(t2, 0);
   cudaError_t e3 = cudaDeviceSynchronize();
   cudaFree(dops);
+  h->ops_ms[0] = h->ops_ms[1] = 0.f;
+  if (e3 == cudaSuccess) {
+    cudaEventElapsedTime(&h->ops_ms[0], t0, t1);
+    cudaEventElapsedTime(&h->ops_ms[1], t1, t2);
+  }
+  h->ops_bytes[0] = brm;
+  h->ops_bytes[1] = bdg;
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  cudaEventDestroy(t2);
   if (e1 != cudaSuccess) return oz::cuda_fail(e1, "operator rowmax");
   if (e2 != cudaSuccess) return oz::cuda_fail(e2, "operator digits");
   if (e3 != cudaSuccess) return oz::cuda_fail(e3, "operator slicing");
@@ -809,7 +833,7 @@ int oz_heff_s::prepare() {
       g.rowmax = this->mB1 + B1row[q]; g.rowexp = this->eB1 + B1row[q];
       g.unit0 = pd; g.unit0m = pm;
       pd += oz::digit_units(g.prows, g.pcols);
-      pm += oz::rowmax_units(g.rows, g.cols);
+      pm += oz::rowmax_units(g.rows, g.cols, g.trans);
       sp.push_back(g);
     }
     for (int q = 0; q < nsec; ++q) {
@@ -896,6 +920,19 @@ extern "C" int heff_apply_host(oz_heff* h, const double* psi_host, double* y_hos
     return rc;
   }
   OZ_CU(cudaMemcpyAsync(y_host, h->dY, (size_t)h->dim * 8, cudaMemcpyDeviceToHost, st));
+  return OZ_OK;
+}
+
+extern "C" int oz_heff_ops_times(const oz_heff* h, float* ms2, long long* bytes2) {
+  if (!h) return fail(OZ_EINVAL, "null handle");
+  if (ms2) {
+    ms2[0] = h->ops_ms[0];
+    ms2[1] = h->ops_ms[1];
+  }
+  if (bytes2) {
+    bytes2[0] = h->ops_bytes[0];
+    bytes2[1] = h->ops_bytes[1];
+  }
   return OZ_OK;
 }
 
@@ -1090,14 +1127,14 @@ int emulated_batch(oz_ctx* c, const std::vector<EmuJob>& jobs, int S, int s, cud
     a.pcols = nkb * KB; a.r0 = 0; a.k0 = 0; a.trans = j.transA; a.S = S; a.scale = 1.0; a.dst = hA + offA[i];
     a.TR = TILE_M; a.nkb = nkb; a.rowmax = mx + rowA[i]; a.rowexp = ex + rowA[i]; a.unit0 = ud; a.unit0m = um;
     ud += digit_units(a.prows, a.pcols);
-    um += rowmax_units(a.rows, a.cols);
+    um += rowmax_units(a.rows, a.cols, a.trans);
     SliceSeg b{};
     b.src = j.B; b.ld = j.ldb; b.rows = j.N; b.cols = j.K; b.prows = (int)(cdiv(j.N, BN) * BN); b.pcols = nkb * KB;
     b.r0 = 0; b.k0 = 0; b.trans = j.transB ? 0 : 1; b.S = S; b.scale = 1.0; b.dst = hB + offB[i]; b.TR = BN;
     b.nkb = nkb;
     b.rowmax = mx + rA + rowB[i]; b.rowexp = ex + rA + rowB[i]; b.unit0 = ud; b.unit0m = um;
     ud += digit_units(b.prows, b.pcols);
-    um += rowmax_units(b.rows, b.cols);
+    um += rowmax_units(b.rows, b.cols, b.trans);
     segs.push_back(a);
     segs.push_back(b);
     GemmProblem P{};

@@ -108,6 +108,8 @@ struct oz_heff_s {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // stage boundaries of the last product
+  float ops_ms[2] = {0.f, 0.f};          // last operator slicing: rowmax pass, digit pass (device ms)
+  long long ops_bytes[2] = {0, 0};       // their algorithmic bytes (read + written)
 
   template <class T>
   int alloc(T** p, size_t bytes) {

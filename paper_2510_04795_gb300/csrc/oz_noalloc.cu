@@ -114,8 +114,8 @@ extern "C" int ozaki_gemm_noalloc(int m, int n, int k, double alpha, const doubl
   b.r0 = 0; b.k0 = 0; b.trans = 1; b.S = S; b.scale = 1.0; b.dst = dB; b.TR = oz::BN; b.nkb = nkb;
   b.rowmax = mx + mpad; b.rowexp = ex + mpad;
   b.unit0 = oz::digit_units(a.prows, a.pcols);
-  b.unit0m = oz::rowmax_units(a.rows, a.cols);
-  const long long um = b.unit0m + oz::rowmax_units(b.rows, b.cols);
+  b.unit0m = oz::rowmax_units(a.rows, a.cols, a.trans);
+  const long long um = b.unit0m + oz::rowmax_units(b.rows, b.cols, b.trans);
   const long long ud = b.unit0 + oz::digit_units(b.prows, b.pcols);
   if ((e = oz::launch_rowmax(nullptr, &pk, 2, um, flags, st)) != cudaSuccess) return fail(OZ_ECUDA, cudaGetErrorString(e));
   if ((e = oz::launch_digits(nullptr, &pk, 2, ud, S, st)) != cudaSuccess) return fail(OZ_ECUDA, cudaGetErrorString(e));

@@ -34,23 +34,76 @@ __device__ __forceinline__ unsigned long long absbits(double v) {
   return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
 }
 
+// Row maxima, two access patterns chosen per segment so that every warp load is coalesced:
+//  * trans == 0 (rows contiguous in memory): one warp per (row, RM_CHUNK columns); lane l reads
+//    columns l, l + 32, ... (256 consecutive bytes per warp load, four loads in flight per lane),
+//    then a warp-shuffle max and one atomicMax per warp;
+//  * trans == 1 (consecutive rows adjacent in memory): one thread per (row, ROWMAX_SPAN
+//    columns), consecutive threads on consecutive rows (256 consecutive bytes per warp load).
+// Segment slot counts are multiples of 32, so no warp straddles two segments.
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
 __global__ void __launch_bounds__(256) rowmax_kernel(const SliceSeg* __restrict__ segs,
                                                      const __grid_constant__ SegPack pack, int nseg, long long total,
                                                      int* __restrict__ flags) {
-  long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= total) return;
+  const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= total) return;  // total is a multiple of 32: whole warps leave together
   const SliceSeg& g = find_seg<true>(segs, pack, nseg, u);
-  long long lu = u - g.unit0m;
-  int i = (int)(lu % g.rows);
-  int sp = (int)(lu / g.rows);
-  int j0 = sp * ROWMAX_SPAN, j1 = min(g.cols, j0 + ROWMAX_SPAN);
+  const long long lu = u - g.unit0m;
   unsigned long long mx = 0;
-  for (int j = j0; j < j1; ++j) {
-    unsigned long long b = absbits(load_src(g, i, j));
-    mx = b > mx ? b : mx;
+  int row = -1;
+  if (!g.trans) {
+    const int lane = (int)(lu & 31);
+    const long long w = lu >> 5;
+    const int nch = (g.cols + RM_CHUNK - 1) / RM_CHUNK;
+    if (w < (long long)g.rows * nch) {
+      row = (int)(w / nch);
+      const int j0 = (int)(w % nch) * RM_CHUNK, j1 = min(g.cols, j0 + RM_CHUNK);
+      const double* rp = g.src + (long long)row * g.ld;
+      const bool sc = g.scale != 1.0;
+      int j = j0 + lane;
+      for (; j + 96 < j1; j += 128) {
+        double v0 = __ldg(rp + j), v1 = __ldg(rp + j + 32), v2 = __ldg(rp + j + 64), v3 = __ldg(rp + j + 96);
+        if (sc) {
+          v0 = __dmul_rn(v0, g.scale);
+          v1 = __dmul_rn(v1, g.scale);
+          v2 = __dmul_rn(v2, g.scale);
+          v3 = __dmul_rn(v3, g.scale);
+        }
+        const unsigned long long b0 = absbits(v0), b1 = absbits(v1), b2 = absbits(v2), b3 = absbits(v3);
+        const unsigned long long m01 = b0 > b1 ? b0 : b1, m23 = b2 > b3 ? b2 : b3;
+        const unsigned long long m = m01 > m23 ? m01 : m23;
+        mx = m > mx ? m : mx;
+      }
+      for (; j < j1; j += 32) {
+        const double v = sc ? __dmul_rn(__ldg(rp + j), g.scale) : __ldg(rp + j);
+        const unsigned long long b = absbits(v);
+        mx = b > mx ? b : mx;
+      }
+    }
+    mx = warp_max_u64(mx);
+    if (lane != 0) return;
+  } else {
+    const long long nsp = (g.cols + ROWMAX_SPAN - 1) / ROWMAX_SPAN;
+    if (lu >= (long long)g.rows * nsp) return;
+    row = (int)(lu % g.rows);
+    const int sp = (int)(lu / g.rows);
+    const int j0 = sp * ROWMAX_SPAN, j1 = min(g.cols, j0 + ROWMAX_SPAN);
+    for (int j = j0; j < j1; ++j) {
+      const unsigned long long b = absbits(load_src(g, row, j));
+      mx = b > mx ? b : mx;
+    }
   }
+  if (row < 0) return;
   if (mx >= 0x7FF0000000000000ull) atomicOr(flags, 1);  // Inf or NaN in the input
-  if (mx) atomicMax(g.rowmax + g.r0 + i, mx);
+  if (mx) atomicMax(g.rowmax + g.r0 + row, mx);
 }
 
 // fixed point of one value: X = RN_even(|x| 2^(8S-1-e)) with sign; S <= 8 (fits int64)
@@ -180,8 +233,11 @@ __global__ void __launch_bounds__(256) digits_kernel(const SliceSeg* __restrict_
   }
 }
 
-long long rowmax_units(int rows, int cols) {
-  return (long long)rows * ((cols + ROWMAX_SPAN - 1) / ROWMAX_SPAN);
+long long rowmax_units(int rows, int cols, int trans) {
+  if (rows <= 0 || cols <= 0) return 0;
+  if (!trans) return 32ll * rows * ((cols + RM_CHUNK - 1) / RM_CHUNK);
+  const long long t = (long long)rows * ((cols + ROWMAX_SPAN - 1) / ROWMAX_SPAN);
+  return (t + 31) / 32 * 32;
 }
 long long digit_units(int prows, int pcols) { return (long long)((prows + 7) / 8) * ((pcols + 7) / 8); }
 

@@ -34,9 +34,11 @@ struct SegPack {
   SliceSeg seg[SEGPACK];
 };
 
-constexpr int ROWMAX_SPAN = 512;  // K elements per rowmax work unit
+constexpr int ROWMAX_SPAN = 512;  // K elements per rowmax thread of a trans = 1 segment
+constexpr int RM_CHUNK = 2048;    // K elements per rowmax warp of a trans = 0 segment
 
-long long rowmax_units(int rows, int cols);
+// rowmax-pass thread slots of a segment (a multiple of 32; unit0m prefixes are sums of these)
+long long rowmax_units(int rows, int cols, int trans);
 long long digit_units(int prows, int pcols);
 // segments from d_segs (device array) or, when d_segs == nullptr, from pack (nseg <= SEGPACK)
 cudaError_t launch_rowmax(const SliceSeg* d_segs, const SegPack* pack, int nseg, long long total, int* flags,

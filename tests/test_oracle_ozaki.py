@@ -176,3 +176,24 @@ def test_alpha_beta():
     C = ozaki.ozaki_gemm(A, B, 7)
     out = ozaki.ozaki_gemm(A, B, 7, alpha=-0.5, beta=2.0, C=C0)
     assert np.array_equal(out, (-0.5 * C) + (2.0 * C0))
+
+
+@pytest.mark.parametrize("S", [1, 2, 3, 5, 7])
+def test_integer_fixed_point_equals_fraction_definition(S):
+    # the int64 form used for S <= 7 against the Fraction form of the same definition: random
+    # magnitudes over 40 binades, exact halfway cases of the rounding, subnormals, zeros, signs
+    rng = np.random.default_rng(100 + S)
+    A = rng.normal(size=(12, 40)) * np.ldexp(1.0, rng.integers(-20, 20, size=(12, 40)))
+    A[0, :8] = 0.0
+    A[1, :] = np.ldexp(rng.integers(1, 2 ** 20, size=40).astype(np.float64), -1074)    # subnormal row
+    A[2, :] = [(k + 0.5) * 2.0 ** -(8 * S - 1) for k in range(-20, 20)]               # ties at the unit
+    A[2, 0] = 0.99                                                                     # sets e = 0
+    A[3, :] = -A[2, :]
+    A[4, 5] = np.nextafter(1.0, 0.0) * 2.0 ** 30
+    e = ozaki.row_exponents(A)
+    X_ref = ozaki.fixed_point(A, e, S)
+    X = ozaki.fixed_point_int(A, e, S)
+    assert all(int(X[i, j]) == int(X_ref[i, j]) for i in range(A.shape[0]) for j in range(A.shape[1]))
+    D_ref = ozaki.digits(X_ref, S)
+    D = ozaki.digits_int(X, S)
+    assert all(np.array_equal(a, b) for a, b in zip(D, D_ref))
