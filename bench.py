@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-validate", action="store_true", help="skip the |dE| check of the two-site sweep")
     p.add_argument("--no-autotune", action="store_true", help="keep the default tile schedule")
     p.add_argument("--no-sweep", action="store_true", help="skip the slice-count sweep on the 40-block workload")
+    p.add_argument("--no-learned", action="store_true", help="skip training and timing the learned level selector")
+    p.add_argument("--learned-structures", type=int, default=3)
     p.add_argument("--no-select", action="store_true",
                    help="skip the informational per-block-level run (analytic selector, 1e-12 budget)")
     return p.parse_args()
@@ -274,6 +276,42 @@ def validation_sweep(ctx, slices: int):
             "sweep_s_gpu": t_gpu, "sweep_s_oracle_cpu": t_or}
 
 
+def train_learned_selector(ctx, args):
+    """The learned slice-level selector for the timed workload: (features, measured error at levels
+    3..8) pairs harvested on the device from products of the same workload family (300 blocks of
+    16-1024, N(0,1) entries) with other structure seeds and 100 terms, the network trained on the
+    device (own forward, backward and Adam kernels).  Returns (net, description)."""
+    import numpy as np
+    import synthetic
+    import paper_2510_04795_gb300 as oz
+    from paper_2510_04795_gb300 import selector
+    t0 = time.perf_counter()
+    rows = []
+    seeds = list(range(11, 11 + args.learned_structures))
+    for sd in seeds:
+        cfg = dict(synthetic.CONFIGS[args.config])
+        cfg["nterms"] = 100
+        st = synthetic.heff_structure(seed=sd, **cfg)
+        Lbuf, Rbuf, Lo, Ro = synthetic.gen_all_task_blocks(st, device="cuda")
+        tasks = [(int(s_), int(d), float(st.term_coef[k]), Lbuf[Lo[i]:Lo[i + 1]].view(int(st.m[d]), int(st.m[s_])),
+                  Rbuf[Ro[i]:Ro[i + 1]].view(int(st.n[d]), int(st.n[s_]))) for i, (k, s_, d) in enumerate(st.tasks)]
+        psi = synthetic.gen_psi(st, device="cuda")
+        hh = oz.Heff(ctx, st.m, st.n, tasks, slices=9, level=8)
+        del tasks, Lbuf, Rbuf
+        rows.append(selector.harvest(hh, psi))
+        hh.close()
+        del psi
+        import torch
+        torch.cuda.empty_cache()
+    X, T, M = (np.concatenate([r[i] for r in rows]) for i in range(3))
+    t1 = time.perf_counter()
+    net = selector.train(X, T, M, epochs=400, batch=64, lr=2e-3, seed=4)
+    t2 = time.perf_counter()
+    return net, {"training_structures": f"seeds {seeds[0]}..{seeds[-1]} of the same family, 100 terms each",
+                 "rows": int(X.shape[0]), "harvest_s": t1 - t0, "train_s": t2 - t1,
+                 "network": "20 -> 64 -> 64 -> 6, tanh, FP32, trained on the device"}
+
+
 def slice_sweep(ctx):
     """The precision dial on the 40-block workload (sizes 8-256, entries N(0,1) 2^-j with j up to 19:
     about six decades of exponent spread inside every block, 128 terms): H_eff psi with s slices for
@@ -368,6 +406,11 @@ def main():
         del hn
         torch.cuda.empty_cache()
 
+    net = None
+    learned_info = None
+    if rank == 0 and not args.no_learned and not args.no_select:
+        net, learned_info = train_learned_selector(ctx, args)
+
     h = oz.Heff(ctx, st.m, st.n, tasks, slices=S)
     ops_ms, ops_bytes = oz.heff_ops_times(h)
     del tasks, Lbuf, Rbuf
@@ -425,9 +468,11 @@ def main():
     # informational, not the headline: the same product with per-block levels picked by the analytic
     # selector for a 1e-12 relative-error budget (the precision dial), then the fixed level restored
     select = None
-    if rank == 0 and not args.no_select:
+    learned = None
+
+    def run_selected(name):
         import collections
-        s1, s2 = h.select_levels(psi, selector="analytic", budget=1e-12)
+        s1, s2 = h.select_levels(psi, selector=name, budget=1e-12, net=net, margin=0.3)
         carrier_sel = h.info()["carrier_flops"]
         ys = torch.empty_like(psi)
         for _ in range(2):
@@ -442,13 +487,22 @@ def main():
         ms_sel = ea.elapsed_time(eb) / args.steps
         ctx.status()
         used = [lv for lv in list(s1) + list(s2) if lv > 0]
-        select = {"selector": "analytic", "budget": 1e-12, "value": F / (ms_sel * 1e-3) / 1e12, "unit": UNIT,
-                  "ms_per_step": ms_sel, "levels": {str(k): v for k, v in sorted(collections.Counter(used).items())},
-                  "carrier_flop_per_step_padded": carrier_sel,
-                  "rel_frobenius_vs_native_fp64": (float(torch.linalg.vector_norm(ys - y_nat) /
-                                                         torch.linalg.vector_norm(y_nat)) if y_nat is not None else None),
-                  "note": "informational; the headline value keeps S = 7 for every product"}
+        res = {"selector": name, "budget": 1e-12, "value": F / (ms_sel * 1e-3) / 1e12, "unit": UNIT,
+               "ms_per_step": ms_sel, "levels": {str(k): v for k, v in sorted(collections.Counter(used).items())},
+               "carrier_flop_per_step_padded": carrier_sel,
+               "rel_frobenius_vs_native_fp64": (float(torch.linalg.vector_norm(ys - y_nat) /
+                                                      torch.linalg.vector_norm(y_nat)) if y_nat is not None else None),
+               "note": "informational; the headline value keeps S = 7 for every product"}
         h.set_levels(None, None)
+        return res
+
+    if rank == 0 and not args.no_select:
+        select = run_selected("analytic")
+        if net is not None:
+            learned = run_selected("learned")
+            learned.update(learned_info)
+            learned["carrier_flop_fixed_s7"] = info["carrier_flops"]
+            net.close()
 
     pk, pk_src = peaks()
     peak = float(pk.get("bf16_tflops_sustained", FALLBACK_PEAK["bf16_tflops_sustained"]))
@@ -538,6 +592,7 @@ def main():
         "davidson": dav,
         "autotune": tuned,
         "per_block_levels": select,
+        "per_block_levels_learned": learned,
         "operator_slicing": ops_slicing,
         "slice_sweep": sweep,
     }

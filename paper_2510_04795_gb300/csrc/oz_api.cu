@@ -350,12 +350,12 @@ int oz_heff_s::enqueue(cudaStream_t st, bool capturing) {
     OZ_CU(cudaEventRecordWithFlags(ev[0], st, evf));
     if (bytes_mB1) OZ_CU(cudaMemsetAsync(mB1, 0, bytes_mB1, st));
     if (bytes_mA2) OZ_CU(cudaMemsetAsync(mA2, 0, bytes_mA2, st));
-    OZ_CU(oz::launch_rowmax(dSegPsi, nullptr, nsegPsi, uPsiM, ctx->d_flags, st));
-    OZ_CU(oz::launch_digits(dSegPsi, nullptr, nsegPsi, uPsiD, S, st));
+    OZ_CU(oz::launch_rowmax(dSegPsi, nullptr, nsegPsi, uPsiM, ctx->d_flags, st, dCtaPsiM));
+    OZ_CU(oz::launch_digits(dSegPsi, nullptr, nsegPsi, uPsiD, S, st, dCtaPsiD));
     OZ_CU(cudaEventRecordWithFlags(ev[1], st, evf));
     OZ_CU(oz::launch_gemm(dP1, dT1, nt1, ctx->nsm, nullptr, s, ctx->d_flags + 1, st, dF1));
     OZ_CU(cudaEventRecordWithFlags(ev[2], st, evf));
-    OZ_CU(oz::launch_digits(dSegA2, nullptr, nsegA2, uA2D, S, st));
+    OZ_CU(oz::launch_digits(dSegA2, nullptr, nsegA2, uA2D, S, st, dCtaA2D));
     if (zero_y) OZ_CU(cudaMemsetAsync(dY, 0, (size_t)dim * 8, st));
     OZ_CU(cudaEventRecordWithFlags(ev[3], st, evf));
     OZ_CU(oz::launch_gemm(dP2, dT2, nt2, ctx->nsm, nullptr, s, ctx->d_flags + 1, st, dF2));
@@ -476,6 +476,17 @@ int slice_ops(oz_heff_s* h, const oz_task* tasks) {
   SliceSeg* dops;
   OZ_CU(cudaMalloc(&dops, ops.size() * sizeof(SliceSeg)));
   cudaMemcpy(dops, ops.data(), ops.size() * sizeof(SliceSeg), cudaMemcpyHostToDevice);
+  const std::vector<int> tm = oz::rowmax_cta_table(ops, um), td = oz::digits_cta_table(ops, ud);
+  int *dtm = nullptr, *dtd = nullptr;
+  cudaError_t ea = cudaMalloc(&dtm, tm.size() * sizeof(int));
+  if (ea == cudaSuccess) ea = cudaMalloc(&dtd, td.size() * sizeof(int));
+  if (ea != cudaSuccess) {
+    cudaFree(dops);
+    cudaFree(dtm);
+    return oz::cuda_fail(ea, "operator slicing tables");
+  }
+  cudaMemcpy(dtm, tm.data(), tm.size() * sizeof(int), cudaMemcpyHostToDevice);
+  cudaMemcpy(dtd, td.data(), td.size() * sizeof(int), cudaMemcpyHostToDevice);
   // algorithmic bytes: the rowmax pass reads every operator element once; the digit pass reads it
   // again and writes S FP16 digits per element of the 8 x 8-padded segment
   long long brm = 0, bdg = 0;
@@ -488,12 +499,14 @@ int slice_ops(oz_heff_s* h, const oz_task* tasks) {
   cudaEventCreate(&t1);
   cudaEventCreate(&t2);
   cudaEventRecord(t0, 0);
-  cudaError_t e1 = oz::launch_rowmax(dops, nullptr, (int)ops.size(), um, c->d_flags, 0);
+  cudaError_t e1 = oz::launch_rowmax(dops, nullptr, (int)ops.size(), um, c->d_flags, 0, dtm);
   cudaEventRecord(t1, 0);
-  cudaError_t e2 = oz::launch_digits(dops, nullptr, (int)ops.size(), ud, S, 0);
+  cudaError_t e2 = oz::launch_digits(dops, nullptr, (int)ops.size(), ud, S, 0, dtd);
   cudaEventRecord(t2, 0);
   cudaError_t e3 = cudaDeviceSynchronize();
   cudaFree(dops);
+  cudaFree(dtm);
+  cudaFree(dtd);
   h->ops_ms[0] = h->ops_ms[1] = 0.f;
   if (e3 == cudaSuccess) {
     cudaEventElapsedTime(&h->ops_ms[0], t0, t1);
@@ -856,6 +869,17 @@ int oz_heff_s::prepare() {
     if ((rc = this->alloc(&this->dSegA2, std::max<size_t>(1, sa.size()) * sizeof(SliceSeg)))) return rc;
     if (!sp.empty()) OZ_CU(cudaMemcpy(this->dSegPsi, sp.data(), sp.size() * sizeof(SliceSeg), cudaMemcpyHostToDevice));
     if (!sa.empty()) OZ_CU(cudaMemcpy(this->dSegA2, sa.data(), sa.size() * sizeof(SliceSeg), cudaMemcpyHostToDevice));
+    // CTA -> first segment tables of the three per-product slicing launches
+    auto upload_table = [&](const std::vector<int>& t, int** dst) -> int {
+      if (int r = this->alloc(dst, std::max<size_t>(1, t.size()) * sizeof(int))) return r;
+      if (!t.empty()) OZ_CU(cudaMemcpy(*dst, t.data(), t.size() * sizeof(int), cudaMemcpyHostToDevice));
+      return OZ_OK;
+    };
+    if (!sp.empty()) {
+      if ((rc = upload_table(oz::rowmax_cta_table(sp, pm), &this->dCtaPsiM))) return rc;
+      if ((rc = upload_table(oz::digits_cta_table(sp, pd), &this->dCtaPsiD))) return rc;
+    }
+    if (!sa.empty() && (rc = upload_table(oz::digits_cta_table(sa, ad), &this->dCtaA2D))) return rc;
   
   }
   // ---- CUDA graph of one product (psi and y are the handle's own buffers)
@@ -1101,8 +1125,16 @@ int emulated_batch(oz_ctx* c, const std::vector<EmuJob>& jobs, int S, int s, cud
   long long ntile = 0;
   for (const EmuJob& j : jobs) ntile += cdiv(j.M, TILE_M) * cdiv(j.N, BN);
   const size_t bT = (size_t)ntile * sizeof(GemmTile);
+  // the CTA -> first segment tables need the unit prefixes: count them first
+  long long umt = 0, udt = 0;
+  for (const EmuJob& j : jobs) {
+    const int nkb = (int)cdiv(j.K, KB);
+    umt += rowmax_units(j.M, j.K, j.transA) + rowmax_units(j.N, j.K, j.transB ? 0 : 1);
+    udt += digit_units((int)(cdiv(j.M, TILE_M) * TILE_M), nkb * KB) + digit_units((int)(cdiv(j.N, BN) * BN), nkb * KB);
+  }
+  const size_t bCm = (size_t)((umt + 255) / 256 + 1) * sizeof(int), bCd = (size_t)((udt + 31) / 32 + 1) * sizeof(int);
   const size_t need = align256(bA) + align256(bB) + align256(bM) + align256(bE) + align256(bS) + align256(bP) +
-                      align256(bT) + 256;
+                      align256(bT) + align256(bCm) + align256(bCd) + 256;
   if (int rc = c->reserve(need)) return rc;
   char* p = c->ws;
   __half* hA = (__half*)p;
@@ -1118,6 +1150,10 @@ int emulated_batch(oz_ctx* c, const std::vector<EmuJob>& jobs, int S, int s, cud
   GemmProblem* dProb = (GemmProblem*)p;
   p += align256(bP);
   GemmTile* dTile = (GemmTile*)p;
+  p += align256(bT);
+  int* dCm = (int*)p;
+  p += align256(bCm);
+  int* dCd = (int*)p;
   long long um = 0, ud = 0;
   for (size_t i = 0; i < n; ++i) {
     const EmuJob& j = jobs[i];
@@ -1148,8 +1184,13 @@ int emulated_batch(oz_ctx* c, const std::vector<EmuJob>& jobs, int S, int s, cud
   OZ_CU(cudaMemcpyAsync(dSeg, segs.data(), bS, cudaMemcpyHostToDevice, st));
   OZ_CU(cudaMemcpyAsync(dProb, probs.data(), bP, cudaMemcpyHostToDevice, st));
   OZ_CU(cudaMemcpyAsync(dTile, tiles.data(), bT, cudaMemcpyHostToDevice, st));
-  OZ_CU(launch_rowmax(dSeg, nullptr, (int)segs.size(), um, c->d_flags, st));
-  OZ_CU(launch_digits(dSeg, nullptr, (int)segs.size(), ud, S, st));
+  const std::vector<int> tcm = rowmax_cta_table(segs, um), tcd = digits_cta_table(segs, ud);
+  if (um != umt || ud != udt || tcm.size() * sizeof(int) > bCm || tcd.size() * sizeof(int) > bCd)
+    return fail(OZ_EINVAL, "emulated batch: inconsistent slicing units");
+  OZ_CU(cudaMemcpyAsync(dCm, tcm.data(), tcm.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  OZ_CU(cudaMemcpyAsync(dCd, tcd.data(), tcd.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  OZ_CU(launch_rowmax(dSeg, nullptr, (int)segs.size(), um, c->d_flags, st, dCm));
+  OZ_CU(launch_digits(dSeg, nullptr, (int)segs.size(), ud, S, st, dCd));
   OZ_CU(launch_gemm(dProb, dTile, (int)tiles.size(), c->nsm, nullptr, s, c->d_flags + 1, st));
   // the host tables above are read by the copies: wait before they go out of scope
   OZ_CU(cudaStreamSynchronize(st));

@@ -65,6 +65,7 @@ struct oz_heff_s {
   oz::GemmTile *dT1 = nullptr, *dT2 = nullptr;
   int nt1 = 0, nt2 = 0;
   oz::SliceSeg *dSegPsi = nullptr, *dSegA2 = nullptr;
+  int *dCtaPsiM = nullptr, *dCtaPsiD = nullptr, *dCtaA2D = nullptr;  // CTA -> first segment tables
   int nsegPsi = 0, nsegA2 = 0;
   long long uPsiM = 0, uPsiD = 0, uA2D = 0;
   bool zero_y = false;

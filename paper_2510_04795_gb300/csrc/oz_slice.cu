@@ -9,13 +9,21 @@
 // Only integer operations touch the values after the (optional) scale multiply.
 #include "oz_slice.cuh"
 
+#include <vector>
+
 namespace oz {
 
+// Segment of a work unit: binary search over the unit prefixes, restricted to the CTA's range
+// [ctaseg[b], ctaseg[b + 1]] when the launch carries that table (launches over many segments).
 template <bool MAXPASS>
 __device__ __forceinline__ const SliceSeg& find_seg(const SliceSeg* segs, const SegPack& pack, int nseg,
-                                                    long long unit) {
+                                                    long long unit, const int* ctaseg) {
   const SliceSeg* base = segs ? segs : pack.seg;
   int lo = 0, hi = nseg - 1;
+  if (ctaseg) {
+    lo = __ldg(ctaseg + blockIdx.x);
+    hi = __ldg(ctaseg + blockIdx.x + 1);
+  }
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
     long long u0 = MAXPASS ? base[mid].unit0m : base[mid].unit0;
@@ -35,9 +43,9 @@ __device__ __forceinline__ unsigned long long absbits(double v) {
 }
 
 // Row maxima, two access patterns chosen per segment so that every warp load is coalesced:
-//  * trans == 0 (rows contiguous in memory): one warp per (row, RM_CHUNK columns); lane l reads
-//    columns l, l + 32, ... (256 consecutive bytes per warp load, four loads in flight per lane),
-//    then a warp-shuffle max and one atomicMax per warp;
+//  * trans == 0 (rows contiguous in memory): one warp per (RM_ROWS rows, RM_CHUNK columns); for
+//    each of its rows lane l reads columns l, l + 32, ... (256 consecutive bytes per warp load,
+//    four loads in flight per lane), then a warp-shuffle max and one atomicMax per row;
 //  * trans == 1 (consecutive rows adjacent in memory): one thread per (row, ROWMAX_SPAN
 //    columns), consecutive threads on consecutive rows (256 consecutive bytes per warp load).
 // Segment slot counts are multiples of 32, so no warp straddles two segments.
@@ -50,24 +58,33 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
   return v;
 }
 
+// *p = max(*p, v) for a maximum that only grows: the atomic is skipped when a plain (L2) read
+// already shows a value >= v.  The rows of a stacked stage-2 operand collect the maxima of many
+// blocks, so most of their updates are skipped instead of serialising on one address.
+__device__ __forceinline__ void max_into(unsigned long long* p, unsigned long long v) {
+  if (v && v > *reinterpret_cast<volatile unsigned long long*>(p)) atomicMax(p, v);
+}
+
 __global__ void __launch_bounds__(256) rowmax_kernel(const SliceSeg* __restrict__ segs,
                                                      const __grid_constant__ SegPack pack, int nseg, long long total,
-                                                     int* __restrict__ flags) {
+                                                     int* __restrict__ flags, const int* __restrict__ ctaseg) {
   const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= total) return;  // total is a multiple of 32: whole warps leave together
-  const SliceSeg& g = find_seg<true>(segs, pack, nseg, u);
+  const SliceSeg& g = find_seg<true>(segs, pack, nseg, u, ctaseg);
   const long long lu = u - g.unit0m;
   unsigned long long mx = 0;
   int row = -1;
   if (!g.trans) {
+    // warp w of the segment: column chunk w % nch of the rows RM_ROWS (w / nch) .. + RM_ROWS - 1
     const int lane = (int)(lu & 31);
     const long long w = lu >> 5;
     const int nch = (g.cols + RM_CHUNK - 1) / RM_CHUNK;
-    if (w < (long long)g.rows * nch) {
-      row = (int)(w / nch);
-      const int j0 = (int)(w % nch) * RM_CHUNK, j1 = min(g.cols, j0 + RM_CHUNK);
-      const double* rp = g.src + (long long)row * g.ld;
-      const bool sc = g.scale != 1.0;
+    const int r0 = (int)(w / nch) * RM_ROWS, r1 = min(g.rows, r0 + RM_ROWS);
+    const int j0 = (int)(w % nch) * RM_CHUNK, j1 = min(g.cols, j0 + RM_CHUNK);
+    const bool sc = g.scale != 1.0;
+    for (int r = r0; r < r1; ++r) {
+      const double* rp = g.src + (long long)r * g.ld;
+      unsigned long long m = 0;
       int j = j0 + lane;
       for (; j + 96 < j1; j += 128) {
         double v0 = __ldg(rp + j), v1 = __ldg(rp + j + 32), v2 = __ldg(rp + j + 64), v3 = __ldg(rp + j + 96);
@@ -79,17 +96,21 @@ __global__ void __launch_bounds__(256) rowmax_kernel(const SliceSeg* __restrict_
         }
         const unsigned long long b0 = absbits(v0), b1 = absbits(v1), b2 = absbits(v2), b3 = absbits(v3);
         const unsigned long long m01 = b0 > b1 ? b0 : b1, m23 = b2 > b3 ? b2 : b3;
-        const unsigned long long m = m01 > m23 ? m01 : m23;
-        mx = m > mx ? m : mx;
+        const unsigned long long mm = m01 > m23 ? m01 : m23;
+        m = mm > m ? mm : m;
       }
       for (; j < j1; j += 32) {
         const double v = sc ? __dmul_rn(__ldg(rp + j), g.scale) : __ldg(rp + j);
         const unsigned long long b = absbits(v);
-        mx = b > mx ? b : mx;
+        m = b > m ? b : m;
+      }
+      m = warp_max_u64(m);
+      if (lane == 0) {
+        if (m >= 0x7FF0000000000000ull) atomicOr(flags, 1);  // Inf or NaN in the input
+        max_into(g.rowmax + g.r0 + r, m);
       }
     }
-    mx = warp_max_u64(mx);
-    if (lane != 0) return;
+    return;
   } else {
     const long long nsp = (g.cols + ROWMAX_SPAN - 1) / ROWMAX_SPAN;
     if (lu >= (long long)g.rows * nsp) return;
@@ -103,7 +124,7 @@ __global__ void __launch_bounds__(256) rowmax_kernel(const SliceSeg* __restrict_
   }
   if (row < 0) return;
   if (mx >= 0x7FF0000000000000ull) atomicOr(flags, 1);  // Inf or NaN in the input
-  if (mx) atomicMax(g.rowmax + g.r0 + row, mx);
+  max_into(g.rowmax + g.r0 + row, mx);
 }
 
 // fixed point of one value: X = RN_even(|x| 2^(8S-1-e)) with sign; S <= 8 (fits int64)
@@ -133,12 +154,13 @@ __device__ __forceinline__ __int128 fixed_point128(double x, int e, int S) {
 
 template <int S>
 __global__ void __launch_bounds__(256) digits_kernel(const SliceSeg* __restrict__ segs,
-                                                     const __grid_constant__ SegPack pack, int nseg, long long total) {
+                                                     const __grid_constant__ SegPack pack, int nseg, long long total,
+                                                     const int* __restrict__ ctaseg) {
   long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   long long u = tid >> 3;
   if (u >= total) return;
   int r8 = (int)(tid & 7);
-  const SliceSeg& g = find_seg<false>(segs, pack, nseg, u);
+  const SliceSeg& g = find_seg<false>(segs, pack, nseg, u, ctaseg);
   long long lu = u - g.unit0;
   int nkc = (g.pcols + 7) >> 3;
   int rg = (int)(lu / nkc), c = (int)(lu % nkc);
@@ -235,20 +257,44 @@ __global__ void __launch_bounds__(256) digits_kernel(const SliceSeg* __restrict_
 
 long long rowmax_units(int rows, int cols, int trans) {
   if (rows <= 0 || cols <= 0) return 0;
-  if (!trans) return 32ll * rows * ((cols + RM_CHUNK - 1) / RM_CHUNK);
+  if (!trans) return 32ll * ((rows + RM_ROWS - 1) / RM_ROWS) * ((cols + RM_CHUNK - 1) / RM_CHUNK);
   const long long t = (long long)rows * ((cols + ROWMAX_SPAN - 1) / ROWMAX_SPAN);
   return (t + 31) / 32 * 32;
 }
 long long digit_units(int prows, int pcols) { return (long long)((prows + 7) / 8) * ((pcols + 7) / 8); }
 
 cudaError_t launch_rowmax(const SliceSeg* d_segs, const SegPack* pack, int nseg, long long total, int* flags,
-                          cudaStream_t st) {
+                          cudaStream_t st, const int* d_ctaseg) {
   if (total <= 0) return cudaSuccess;
   SegPack p{};
   if (!d_segs) p = *pack;
   long long blocks = (total + 255) / 256;
-  rowmax_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_segs, p, nseg, total, flags);
+  rowmax_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_segs, p, nseg, total, flags, d_ctaseg);
   return cudaGetLastError();
+}
+
+// CTA -> first segment tables of the two slicing launches: CTA b of the rowmax launch covers the
+// thread slots [256 b, 256 b + 256), CTA b of the digit launch the units [32 b, 32 b + 32); entry
+// b is the segment holding the CTA's first slot or unit, and the last entry is nseg - 1.
+static std::vector<int> cta_table(const std::vector<SliceSeg>& segs, long long total, long long per_cta,
+                                  bool maxpass) {
+  const long long nb = (total + per_cta - 1) / per_cta;
+  std::vector<int> t((size_t)nb + 1);
+  int k = 0;
+  const int n = (int)segs.size();
+  for (long long b = 0; b < nb; ++b) {
+    const long long u = b * per_cta;
+    while (k + 1 < n && (maxpass ? segs[k + 1].unit0m : segs[k + 1].unit0) <= u) ++k;
+    t[(size_t)b] = k;
+  }
+  t[(size_t)nb] = n - 1;
+  return t;
+}
+std::vector<int> rowmax_cta_table(const std::vector<SliceSeg>& segs, long long total) {
+  return cta_table(segs, total, 256, true);
+}
+std::vector<int> digits_cta_table(const std::vector<SliceSeg>& segs, long long total) {
+  return cta_table(segs, total, 32, false);
 }
 
 __global__ void untile_kernel(const __half* __restrict__ dig, int TR, int nkb, int S, int rows, int cols,
@@ -273,13 +319,13 @@ cudaError_t launch_untile(const __half* dig, int TR, int nkb, int S, int rows, i
 }
 
 cudaError_t launch_digits(const SliceSeg* d_segs, const SegPack* pack, int nseg, long long total, int S,
-                          cudaStream_t st) {
+                          cudaStream_t st, const int* d_ctaseg) {
   if (total <= 0) return cudaSuccess;
   SegPack p{};
   if (!d_segs) p = *pack;
   long long blocks = (total * 8 + 255) / 256;
   switch (S) {
-#define OZ_CASE(s) case s: digits_kernel<s><<<(unsigned)blocks, 256, 0, st>>>(d_segs, p, nseg, total); break;
+#define OZ_CASE(s) case s: digits_kernel<s><<<(unsigned)blocks, 256, 0, st>>>(d_segs, p, nseg, total, d_ctaseg); break;
     OZ_CASE(1) OZ_CASE(2) OZ_CASE(3) OZ_CASE(4) OZ_CASE(5) OZ_CASE(6) OZ_CASE(7) OZ_CASE(8) OZ_CASE(9)
 #undef OZ_CASE
     default: return cudaErrorInvalidValue;

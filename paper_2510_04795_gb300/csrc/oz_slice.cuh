@@ -1,6 +1,8 @@
 // Slicing: FP64 rectangles -> shared exponents + balanced INT8 digits stored as FP16 in
 // pre-tiled tcgen05 operand layout.
 #pragma once
+#include <vector>
+
 #include "oz_common.cuh"
 
 namespace oz {
@@ -36,15 +38,20 @@ struct SegPack {
 
 constexpr int ROWMAX_SPAN = 512;  // K elements per rowmax thread of a trans = 1 segment
 constexpr int RM_CHUNK = 2048;    // K elements per rowmax warp of a trans = 0 segment
+constexpr int RM_ROWS = 8;        // rows per rowmax warp of a trans = 0 segment
 
 // rowmax-pass thread slots of a segment (a multiple of 32; unit0m prefixes are sums of these)
 long long rowmax_units(int rows, int cols, int trans);
 long long digit_units(int prows, int pcols);
-// segments from d_segs (device array) or, when d_segs == nullptr, from pack (nseg <= SEGPACK)
+// segments from d_segs (device array) or, when d_segs == nullptr, from pack (nseg <= SEGPACK);
+// d_ctaseg (optional, device) = the launch's CTA -> first segment table (rowmax_cta_table /
+// digits_cta_table of the same segments and total), which bounds each thread's segment search
 cudaError_t launch_rowmax(const SliceSeg* d_segs, const SegPack* pack, int nseg, long long total, int* flags,
-                          cudaStream_t st);
+                          cudaStream_t st, const int* d_ctaseg = nullptr);
 cudaError_t launch_digits(const SliceSeg* d_segs, const SegPack* pack, int nseg, long long total, int S,
-                          cudaStream_t st);
+                          cudaStream_t st, const int* d_ctaseg = nullptr);
+std::vector<int> rowmax_cta_table(const std::vector<SliceSeg>& segs, long long total);
+std::vector<int> digits_cta_table(const std::vector<SliceSeg>& segs, long long total);
 // untile digits of rows [0,rows) x [0,cols) of an A-role operand into int8 d_out[t][i][j]
 cudaError_t launch_untile(const __half* dig, int TR, int nkb, int S, int rows, int cols, int8_t* out,
                           cudaStream_t st);
