@@ -29,8 +29,8 @@ FALLBACK_PEAK = {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gb
 
 # DRAM bytes per algorithmic carrier flop of the GEMM kernel, from one ncu capture, and the
 # digest of the kernel source it was taken on (the figure is dropped once the source changes).
-NCU_TRAFFIC = {"bytes_per_carrier_flop": 0.0021553,
-               "gemm_source_sha256": "8b203552428f787137da40d4386f53a6b8e91cad1abd6d24da0c07f75289f662"}
+NCU_TRAFFIC = {"bytes_per_carrier_flop": 0.0021531,
+               "gemm_source_sha256": "fcfed12a27c9d88e4f92d33603fb36ba68a6a0b51eef92d954b03f58baf1962c"}
 
 
 def parse():

@@ -49,6 +49,14 @@ __device__ __forceinline__ unsigned long long absbits(double v) {
 //  * trans == 1 (consecutive rows adjacent in memory): one thread per (row, ROWMAX_SPAN
 //    columns), consecutive threads on consecutive rows (256 consecutive bytes per warp load).
 // Segment slot counts are multiples of 32, so no warp straddles two segments.
+// Bit pattern of max_j |RN(c x_j)| from that of max_j |x_j|: rounding is monotonic, so the maximum of
+// the scaled magnitudes is the scaled maximum, RN(|c| max_j |x_j|) -- one multiply per row instead of
+// one per element.  NaN and Inf patterns pass through (their products stay non-finite).
+__device__ __forceinline__ unsigned long long scaled_max(unsigned long long mb, double c) {
+  if (c == 1.0 || mb == 0ull) return mb;
+  return absbits(__dmul_rn(__longlong_as_double((long long)mb), fabs(c)));
+}
+
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -56,13 +64,6 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     v = w > v ? w : v;
   }
   return v;
-}
-
-// *p = max(*p, v) for a maximum that only grows: the atomic is skipped when a plain (L2) read
-// already shows a value >= v.  The rows of a stacked stage-2 operand collect the maxima of many
-// blocks, so most of their updates are skipped instead of serialising on one address.
-__device__ __forceinline__ void max_into(unsigned long long* p, unsigned long long v) {
-  if (v && v > *reinterpret_cast<volatile unsigned long long*>(p)) atomicMax(p, v);
 }
 
 __global__ void __launch_bounds__(256) rowmax_kernel(const SliceSeg* __restrict__ segs,
@@ -81,33 +82,25 @@ __global__ void __launch_bounds__(256) rowmax_kernel(const SliceSeg* __restrict_
     const int nch = (g.cols + RM_CHUNK - 1) / RM_CHUNK;
     const int r0 = (int)(w / nch) * RM_ROWS, r1 = min(g.rows, r0 + RM_ROWS);
     const int j0 = (int)(w % nch) * RM_CHUNK, j1 = min(g.cols, j0 + RM_CHUNK);
-    const bool sc = g.scale != 1.0;
     for (int r = r0; r < r1; ++r) {
       const double* rp = g.src + (long long)r * g.ld;
       unsigned long long m = 0;
       int j = j0 + lane;
       for (; j + 96 < j1; j += 128) {
-        double v0 = __ldg(rp + j), v1 = __ldg(rp + j + 32), v2 = __ldg(rp + j + 64), v3 = __ldg(rp + j + 96);
-        if (sc) {
-          v0 = __dmul_rn(v0, g.scale);
-          v1 = __dmul_rn(v1, g.scale);
-          v2 = __dmul_rn(v2, g.scale);
-          v3 = __dmul_rn(v3, g.scale);
-        }
-        const unsigned long long b0 = absbits(v0), b1 = absbits(v1), b2 = absbits(v2), b3 = absbits(v3);
+        const unsigned long long b0 = absbits(__ldg(rp + j)), b1 = absbits(__ldg(rp + j + 32));
+        const unsigned long long b2 = absbits(__ldg(rp + j + 64)), b3 = absbits(__ldg(rp + j + 96));
         const unsigned long long m01 = b0 > b1 ? b0 : b1, m23 = b2 > b3 ? b2 : b3;
         const unsigned long long mm = m01 > m23 ? m01 : m23;
         m = mm > m ? mm : m;
       }
       for (; j < j1; j += 32) {
-        const double v = sc ? __dmul_rn(__ldg(rp + j), g.scale) : __ldg(rp + j);
-        const unsigned long long b = absbits(v);
+        const unsigned long long b = absbits(__ldg(rp + j));
         m = b > m ? b : m;
       }
-      m = warp_max_u64(m);
+      m = scaled_max(warp_max_u64(m), g.scale);
       if (lane == 0) {
         if (m >= 0x7FF0000000000000ull) atomicOr(flags, 1);  // Inf or NaN in the input
-        max_into(g.rowmax + g.r0 + r, m);
+        if (m) atomicMax(g.rowmax + g.r0 + r, m);
       }
     }
     return;
@@ -118,13 +111,14 @@ __global__ void __launch_bounds__(256) rowmax_kernel(const SliceSeg* __restrict_
     const int sp = (int)(lu / g.rows);
     const int j0 = sp * ROWMAX_SPAN, j1 = min(g.cols, j0 + ROWMAX_SPAN);
     for (int j = j0; j < j1; ++j) {
-      const unsigned long long b = absbits(load_src(g, row, j));
+      const unsigned long long b = absbits(__ldg(g.src + (long long)j * g.ld + row));
       mx = b > mx ? b : mx;
     }
+    mx = scaled_max(mx, g.scale);
   }
   if (row < 0) return;
   if (mx >= 0x7FF0000000000000ull) atomicOr(flags, 1);  // Inf or NaN in the input
-  max_into(g.rowmax + g.r0 + row, mx);
+  if (mx) atomicMax(g.rowmax + g.r0 + row, mx);
 }
 
 // fixed point of one value: X = RN_even(|x| 2^(8S-1-e)) with sign; S <= 8 (fits int64)
