@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--no-autotune", action="store_true", help="keep the default tile schedule")
     p.add_argument("--no-sweep", action="store_true", help="skip the slice-count sweep on the 40-block workload")
     p.add_argument("--no-learned", action="store_true", help="skip training and timing the learned level selector")
+    p.add_argument("--no-shapes", action="store_true", help="skip timing the CTA-pair tile shape")
     p.add_argument("--learned-structures", type=int, default=3)
     p.add_argument("--no-select", action="store_true",
                    help="skip the informational per-block-level run (analytic selector, 1e-12 budget)")
@@ -406,6 +407,34 @@ def main():
         del hn
         torch.cuda.empty_cache()
 
+    # the other tile shape of the products, for the record: 256 x 64 tiles on CTA pairs (the handle's
+    # default is one CTA per 128 x 64 tile); timed on the same operators, then freed
+    tile_shapes = None
+    if rank == 0 and not args.no_shapes:
+        hp = oz.Heff(ctx, st.m, st.n, tasks, slices=S, tile="pair")
+        yp = hp.apply(psi)
+        for _ in range(2):
+            hp.apply(psi, yp)
+        torch.cuda.synchronize()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record()
+        st_p = [0.0] * 4
+        for _ in range(args.steps):
+            hp.apply(psi, yp)
+            for i, v in enumerate(oz.heff_stage_times(hp)):
+                st_p[i] += v
+        eb.record()
+        torch.cuda.synchronize()
+        ctx.status()
+        tile_shapes = {"pair_256x64": {"ms_per_step": ea.elapsed_time(eb) / args.steps,
+                                       "gemm_stage1_ms": st_p[1] / args.steps, "gemm_stage2_ms": st_p[3] / args.steps,
+                                       "carrier_flop_per_step_padded": hp.info()["carrier_flops"],
+                                       "schedule": "balanced"}}
+        y_pair = yp.cpu()
+        hp.close()
+        del hp, yp
+        torch.cuda.empty_cache()
+
     net = None
     learned_info = None
     if rank == 0 and not args.no_learned and not args.no_select:
@@ -422,6 +451,8 @@ def main():
                  "stage2": ["balanced", "balanced_asc", "strided"][s2],
                  "ms_per_schedule": [[round(a, 3), round(b, 3)] for a, b in tms]}
     info = h.info()
+    if tile_shapes is not None:
+        tile_shapes["chosen"] = "cta_128x64" if info["tile"] == 1 else "pair_256x64"
     y = torch.empty_like(psi)
     for _ in range(args.warmup):
         h.apply(psi, y)
@@ -447,6 +478,11 @@ def main():
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
     ctx.status()
     stage = [v / args.steps for v in stage]
+    if tile_shapes is not None:
+        tile_shapes["cta_128x64"] = {"ms_per_step": ms, "gemm_stage1_ms": stage[1], "gemm_stage2_ms": stage[3],
+                                     "carrier_flop_per_step_padded": info["carrier_flops"],
+                                     "schedule": tuned and [tuned["stage1"], tuned["stage2"]]}
+        tile_shapes["results_equal"] = bool(torch.equal(y.cpu(), y_pair))
 
     # accuracy against the native FP64 product of the same task list
     rel_native = None
@@ -593,6 +629,7 @@ def main():
         "autotune": tuned,
         "per_block_levels": select,
         "per_block_levels_learned": learned,
+        "tile_shapes": tile_shapes,
         "operator_slicing": ops_slicing,
         "slice_sweep": sweep,
     }

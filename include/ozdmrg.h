@@ -59,7 +59,15 @@ typedef struct oz_prec {
   int slices; /* S: digits stored per value, 1..9 */
   int level;  /* s: digits used, 1..min(S, 8); 0 means s = S */
   int mode;   /* OZ_MODE_EAGER or OZ_MODE_NATIVE (OZ_MODE_PERFORMANT: ozaki_gemm only) */
+  int tile;   /* H_eff handles: OZ_TILE_AUTO (0), OZ_TILE_CTA (128 x 64 tiles, one CTA each) or
+                 OZ_TILE_PAIR (256 x 64 tiles on a CTA pair: one MMA issuer for two SMs); AUTO
+                 takes OZ_TILE_CTA, the faster of the two on GB300 (OZ_EINVAL for OZ_TILE_PAIR on a
+                 device without clusters of two).  Results are identical.  Other entry points
+                 ignore it. */
 } oz_prec;
+#define OZ_TILE_AUTO 0
+#define OZ_TILE_CTA 1
+#define OZ_TILE_PAIR 2
 
 typedef void* oz_stream_t; /* a cudaStream_t (0 = legacy default stream) */
 
@@ -201,6 +209,8 @@ typedef struct oz_heff_info {
   long long bytes_scratch;/* device bytes of per-product scratch */
   long long gemm1_tiles, gemm2_tiles;
   int slices, level, mode;
+  int tile;               /* OZ_TILE_CTA or OZ_TILE_PAIR: the GEMM tiles of the products */
+  int units;              /* persistent units of the GEMM launches: CTAs, or CTA pairs */
 } oz_heff_info;
 int oz_heff_info_get(const oz_heff* h, oz_heff_info* out);
 /* Per-block precision dial (emulated handles): s1[q] = slice level of the stage-1 product of

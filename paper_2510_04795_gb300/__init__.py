@@ -34,9 +34,10 @@ def _stream(stream) -> C.c_void_p:
     return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
 
 
-def _prec(slices: int, level: int, mode) -> N.oz_prec:
+def _prec(slices: int, level: int, mode, tile="auto") -> N.oz_prec:
     m = {"eager": OZ_MODE_EAGER, "native": OZ_MODE_NATIVE, "performant": N.OZ_MODE_PERFORMANT}.get(mode, mode)
-    return N.oz_prec(int(slices), int(level), int(m))
+    t = {"auto": N.OZ_TILE_AUTO, "cta": N.OZ_TILE_CTA, "pair": N.OZ_TILE_PAIR}.get(tile, tile)
+    return N.oz_prec(int(slices), int(level), int(m), int(t))
 
 
 def _check_f64(*ts):
@@ -141,7 +142,9 @@ class Heff:
     R (n[dst] x n[src]) CUDA float64 tensors (kept alive by the handle in native mode).
     """
 
-    def __init__(self, ctx: Context, m, n, tasks, slices=7, level=0, mode="eager"):
+    def __init__(self, ctx: Context, m, n, tasks, slices=7, level=0, mode="eager", tile="auto"):
+        """``tile``: "cta" (128 x 64 tiles, one CTA each), "pair" (256 x 64 tiles on CTA pairs) or
+        "auto" (= "cta", the faster on GB300); the results are identical."""
         self.ctx = ctx
         self.lib = ctx.lib
         self.m = [int(x) for x in m]
@@ -150,7 +153,7 @@ class Heff:
         arr = _task_array(tasks)
         mm = (C.c_int * nsec)(*self.m)
         nn = (C.c_int * nsec)(*self.n)
-        p = _prec(slices, level, mode)
+        p = _prec(slices, level, mode, tile)
         h = C.c_void_p()
         N.check(self.lib.oz_heff_create(ctx.h, nsec, mm, nn, len(tasks), arr, C.byref(p), C.byref(h)))
         self.h = h

@@ -25,7 +25,10 @@ class OzError(RuntimeError):
 
 
 class oz_prec(C.Structure):
-    _fields_ = [("slices", C.c_int), ("level", C.c_int), ("mode", C.c_int)]
+    _fields_ = [("slices", C.c_int), ("level", C.c_int), ("mode", C.c_int), ("tile", C.c_int)]
+
+
+OZ_TILE_AUTO, OZ_TILE_CTA, OZ_TILE_PAIR = 0, 1, 2
 
 
 class oz_task(C.Structure):
@@ -35,7 +38,8 @@ class oz_task(C.Structure):
 class oz_heff_info(C.Structure):
     _fields_ = [("dim", C.c_longlong), ("flops", C.c_longlong), ("carrier_flops", C.c_longlong),
                 ("bytes_ops", C.c_longlong), ("bytes_scratch", C.c_longlong), ("gemm1_tiles", C.c_longlong),
-                ("gemm2_tiles", C.c_longlong), ("slices", C.c_int), ("level", C.c_int), ("mode", C.c_int)]
+                ("gemm2_tiles", C.c_longlong), ("slices", C.c_int), ("level", C.c_int), ("mode", C.c_int),
+                ("tile", C.c_int), ("units", C.c_int)]
 
 
 class oz_dmrg_step(C.Structure):

@@ -353,12 +353,12 @@ int oz_heff_s::enqueue(cudaStream_t st, bool capturing) {
     OZ_CU(oz::launch_rowmax(dSegPsi, nullptr, nsegPsi, uPsiM, ctx->d_flags, st, dCtaPsiM));
     OZ_CU(oz::launch_digits(dSegPsi, nullptr, nsegPsi, uPsiD, S, st, dCtaPsiD));
     OZ_CU(cudaEventRecordWithFlags(ev[1], st, evf));
-    OZ_CU(oz::launch_gemm(dP1, dT1, nt1, ctx->nsm, nullptr, s, ctx->d_flags + 1, st, dF1));
+    OZ_CU(oz::launch_gemm(dP1, dT1, nt1, units, nullptr, s, ctx->d_flags + 1, st, dF1, pair));
     OZ_CU(cudaEventRecordWithFlags(ev[2], st, evf));
     OZ_CU(oz::launch_digits(dSegA2, nullptr, nsegA2, uA2D, S, st, dCtaA2D));
     if (zero_y) OZ_CU(cudaMemsetAsync(dY, 0, (size_t)dim * 8, st));
     OZ_CU(cudaEventRecordWithFlags(ev[3], st, evf));
-    OZ_CU(oz::launch_gemm(dP2, dT2, nt2, ctx->nsm, nullptr, s, ctx->d_flags + 1, st, dF2));
+    OZ_CU(oz::launch_gemm(dP2, dT2, nt2, units, nullptr, s, ctx->d_flags + 1, st, dF2, pair));
     OZ_CU(cudaEventRecordWithFlags(ev[4], st, evf));
     return OZ_OK;
   }
@@ -392,16 +392,17 @@ namespace {
 long long carrier_flops_of(int nsec, const int* m, const int* n, const std::vector<int>& rows1,
                            const std::vector<int>& nkb1, const std::vector<int>& nkb2,
                            const std::vector<std::vector<int>>& bysrc, const std::vector<std::vector<int>>& bydst,
-                           const std::vector<int>& lev1, const std::vector<int>& lev2, const std::vector<char>& swap2) {
+                           const std::vector<int>& lev1, const std::vector<int>& lev2, const std::vector<char>& swap2,
+                           int TM) {
   long long f = 0;
   for (int q = 0; q < nsec; ++q) {
     const long long P1 = (long long)lev1[q] * (lev1[q] + 1) / 2, P2 = (long long)lev2[q] * (lev2[q] + 1) / 2;
     if (!bysrc[q].empty())
-      f += P1 * 2 * (cdiv(rows1[q], oz::TILE_M) * oz::TILE_M) * (cdiv(n[q], oz::BN) * oz::BN) *
+      f += P1 * 2 * (cdiv(rows1[q], TM) * TM) * (cdiv(n[q], oz::BN) * oz::BN) *
            ((long long)nkb1[q] * oz::KB);
     if (!bydst[q].empty()) {
       const long long r2 = swap2[q] ? n[q] : m[q], c2 = swap2[q] ? m[q] : n[q];
-      f += P2 * 2 * (cdiv(r2, oz::TILE_M) * oz::TILE_M) * (cdiv(c2, oz::BN) * oz::BN) * ((long long)nkb2[q] * oz::KB);
+      f += P2 * 2 * (cdiv(r2, TM) * TM) * (cdiv(c2, oz::BN) * oz::BN) * ((long long)nkb2[q] * oz::KB);
     }
   }
   return f;
@@ -463,6 +464,7 @@ int slice_ops(oz_heff_s* h, const oz_task* tasks) {
       g.src = tk.d_R; g.ld = n[tk.src]; g.rows = n[q]; g.cols = n[tk.src]; g.prows = g.rows; g.pcols = g.cols;
       g.r0 = 0; g.k0 = (int)h->offk[t]; g.trans = 0; g.S = S; g.scale = tk.coef;
       g.dst = h->dB2 + h->B2off[q]; g.TR = h->swap2[q] ? oz::TILE_M : oz::BN; g.nkb = h->nkb2[q];
+      g.half_major = h->pair && !h->swap2[q] ? 1 : 0;
       g.rowmax = h->mB2 + h->B2row[q]; g.rowexp = h->eB2 + h->B2row[q];
       g.unit0 = ud; g.unit0m = um;
       ud += oz::digit_units(g.prows, g.pcols);
@@ -545,9 +547,17 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
       return fail(OZ_EINVAL, "task sector out of range");
     if (!tasks[t].d_L || !tasks[t].d_R) return fail(OZ_EINVAL, "task block pointer is null");
   }
+  if (prec->tile < OZ_TILE_AUTO || prec->tile > OZ_TILE_PAIR) return fail(OZ_EINVAL, "unknown tile choice");
   OZ_CU(cudaSetDevice(c->device));
+  // products on CTA pairs on request (emulated handles only); OZ_TILE_AUTO takes one CTA per tile,
+  // which measured faster on GB300 for both stages of the 300-block workload
+  int pair_units = 0;
+  if (mode == OZ_MODE_EAGER && prec->tile == OZ_TILE_PAIR) pair_units = oz::gemm_pair_units(c->nsm);
+  if (prec->tile == OZ_TILE_PAIR && pair_units <= 0) return fail(OZ_EINVAL, "this device runs no CTA pairs");
   oz_heff* h = new oz_heff_s();
   h->ctx = c;
+  h->pair = pair_units > 0;
+  h->units = h->pair ? pair_units : c->nsm;
   h->nsec = nsec;
   h->ntask = ntask;
   h->S = S;
@@ -600,16 +610,20 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
   const long long A1tile = (long long)oz::TILE_M * oz::KB, Btile = (long long)oz::BN * oz::KB;
   std::vector<long long> A1off(nsec + 1, 0), B1off(nsec + 1, 0), A2off(nsec + 1, 0), B2off(nsec + 1, 0);
   std::vector<long long> A1row(nsec + 1, 0), B1row(nsec + 1, 0), A2row(nsec + 1, 0), B2row(nsec + 1, 0);
+  // rows of a tile's M side: 128, or 256 on a CTA pair (the orientation of stage 2 weighs the
+  // padding of that tile)
+  const int TMt = h->pair ? 2 * oz::TILE_M : oz::TILE_M;
+  auto a_tiles = [&](long long rows) { return cdiv(rows, oz::TILE_M); };
   h->swap2.assign(nsec, 0);
   for (int q = 0; q < nsec; ++q)
-    h->swap2[q] = cdiv(n[q], oz::TILE_M) * oz::TILE_M * cdiv(m[q], oz::BN) * oz::BN <
-                  cdiv(m[q], oz::TILE_M) * oz::TILE_M * cdiv(n[q], oz::BN) * oz::BN;
+    h->swap2[q] = cdiv(n[q], TMt) * TMt * cdiv(m[q], oz::BN) * oz::BN < cdiv(m[q], TMt) * TMt * cdiv(n[q], oz::BN) * oz::BN;
   for (int q = 0; q < nsec; ++q) {
-    long long nrbA1 = cdiv(rows1[q], oz::TILE_M), nrbB1 = cdiv(n[q], oz::BN);
+    long long nrbA1 = a_tiles(rows1[q]), nrbB1 = cdiv(n[q], oz::BN);
     // stage 2: T (m[q] rows) and the (cR) stack (n[q] rows) take the 128- and 64-row sides of the
     // tile, or the other way round when the handle computes this sector transposed
     const long long trA2 = h->swap2[q] ? oz::BN : oz::TILE_M, trB2 = h->swap2[q] ? oz::TILE_M : oz::BN;
-    long long nrbA2 = cdiv(m[q], trA2), nrbB2 = cdiv(n[q], trB2);
+    long long nrbA2 = h->swap2[q] ? cdiv(m[q], trA2) : a_tiles(m[q]);
+    long long nrbB2 = h->swap2[q] ? a_tiles(n[q]) : cdiv(n[q], trB2);
     A1off[q + 1] = A1off[q] + nrbA1 * nkb1[q] * S * A1tile;
     B1off[q + 1] = B1off[q] + nrbB1 * nkb1[q] * S * Btile;
     A2off[q + 1] = A2off[q] + nrbA2 * nkb2[q] * S * trA2 * oz::KB;
@@ -619,7 +633,7 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
     A2row[q + 1] = A2row[q] + nrbA2 * trA2;
     B2row[q + 1] = B2row[q] + nrbB2 * trB2;
   }
-  h->carrier_flops = carrier_flops_of(nsec, m, n, rows1, nkb1, nkb2, bysrc, bydst, h->lev1, h->lev2, h->swap2);
+  h->carrier_flops = carrier_flops_of(nsec, m, n, rows1, nkb1, nkb2, bysrc, bydst, h->lev1, h->lev2, h->swap2, TMt);
 
   int rc;
   h->bytes_scratch = (long long)stoff[nsec] * 8 + 2 * h->dim * 8;
@@ -805,13 +819,14 @@ int oz_heff_s::prepare() {
         this->p2sec.push_back(q);
       }
     }
-    auto make_tiles = [](const std::vector<GemmProblem>& ps) {
+    const int TMt = this->pair ? 2 * oz::TILE_M : oz::TILE_M;  // tile rows: one CTA, or a CTA pair
+    auto make_tiles = [TMt](const std::vector<GemmProblem>& ps) {
       std::vector<int> ord(ps.size());
       for (size_t i = 0; i < ps.size(); ++i) ord[i] = (int)i;
       std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return ps[a].nkb > ps[b].nkb; });
       std::vector<GemmTile> tl;
       for (int pi : ord) {
-        int nrb = (int)cdiv(ps[pi].M, oz::TILE_M), nnb = (int)cdiv(ps[pi].N, oz::BN);
+        int nrb = (int)cdiv(ps[pi].M, TMt), nnb = (int)cdiv(ps[pi].N, oz::BN);
         for (int mb = 0; mb < nrb; ++mb)
           for (int nb = 0; nb < nnb; ++nb) tl.push_back({pi, mb, nb, 0});
       }
@@ -842,7 +857,7 @@ int oz_heff_s::prepare() {
       SliceSeg g{};
       g.src = this->dPsi + this->psioff[q]; g.ld = n[q]; g.rows = n[q]; g.cols = m[q]; g.prows = g.rows; g.pcols = g.cols;
       g.r0 = 0; g.k0 = 0; g.trans = 1; g.S = S; g.scale = 1.0;
-      g.dst = this->dB1 + B1off[q]; g.TR = oz::BN; g.nkb = nkb1[q];
+      g.dst = this->dB1 + B1off[q]; g.TR = oz::BN; g.nkb = nkb1[q]; g.half_major = this->pair ? 1 : 0;
       g.rowmax = this->mB1 + B1row[q]; g.rowexp = this->eB1 + B1row[q];
       g.unit0 = pd; g.unit0m = pm;
       pd += oz::digit_units(g.prows, g.pcols);
@@ -855,6 +870,7 @@ int oz_heff_s::prepare() {
       g.src = this->dStage + stoff[q]; g.ld = ld2[q]; g.rows = m[q]; g.cols = ld2[q]; g.prows = g.rows;
       g.pcols = g.cols; g.r0 = 0; g.k0 = 0; g.trans = 0; g.S = S; g.scale = 1.0;
       g.dst = this->dA2 + A2off[q]; g.TR = swap2[q] ? oz::BN : oz::TILE_M; g.nkb = nkb2[q];
+      g.half_major = this->pair && swap2[q] ? 1 : 0;
       g.rowmax = this->mA2 + A2row[q]; g.rowexp = this->eA2 + A2row[q];
       g.unit0 = ad; g.unit0m = 0;
       ad += oz::digit_units(g.prows, g.pcols);
@@ -980,6 +996,8 @@ extern "C" int oz_heff_info_get(const oz_heff* h, oz_heff_info* o) {
   o->slices = h->S;
   o->level = h->s;
   o->mode = h->mode;
+  o->tile = h->pair ? OZ_TILE_PAIR : OZ_TILE_CTA;
+  o->units = h->units;
   return OZ_OK;
 }
 
@@ -1019,7 +1037,8 @@ int oz_heff_s::set_levels(const int* s1, const int* s2) {
   if (!hp1.empty()) OZ_CU(cudaMemcpy(dP1, hp1.data(), hp1.size() * sizeof(GemmProblem), cudaMemcpyHostToDevice));
   if (!hp2.empty()) OZ_CU(cudaMemcpy(dP2, hp2.data(), hp2.size() * sizeof(GemmProblem), cudaMemcpyHostToDevice));
   if (int rc = balance()) return rc;
-  carrier_flops = carrier_flops_of(nsec, m.data(), n.data(), rows1, nkb1, nkb2, bysrc, bydst, lev1, lev2, swap2);
+  carrier_flops = carrier_flops_of(nsec, m.data(), n.data(), rows1, nkb1, nkb2, bysrc, bydst, lev1, lev2, swap2,
+                                   pair ? 2 * oz::TILE_M : oz::TILE_M);
   return OZ_OK;
 }
 
@@ -1043,8 +1062,8 @@ int oz_heff_s::balance() {
   std::vector<int> f1, f2;
   ht1 = bt1;
   ht2 = bt2;
-  oz::schedule_tiles(hp1, ht1, ctx->nsm, sched1, f1);
-  oz::schedule_tiles(hp2, ht2, ctx->nsm, sched2, f2);
+  oz::schedule_tiles(hp1, ht1, units, sched1, f1);
+  oz::schedule_tiles(hp2, ht2, units, sched2, f2);
   if (!ht1.empty()) OZ_CU(cudaMemcpy(dT1, ht1.data(), ht1.size() * sizeof(GemmTile), cudaMemcpyHostToDevice));
   if (!ht2.empty()) OZ_CU(cudaMemcpy(dT2, ht2.data(), ht2.size() * sizeof(GemmTile), cudaMemcpyHostToDevice));
   OZ_CU(cudaMemcpy(dF1, f1.data(), f1.size() * 4, cudaMemcpyHostToDevice));

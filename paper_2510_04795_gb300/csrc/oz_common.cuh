@@ -128,6 +128,72 @@ OZ_DEVICE_INLINE void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t id, u
         "l"(a), "l"(b), "r"(id), "r"(acc));
 }
 
+// ---- CTA pairs (cta_group::2): one MMA of M = 256 over two CTAs of a cluster of 2.  CTA rank r
+// supplies rows 128 r .. 128 r + 127 of A and rows N/2 r .. N/2 r + N/2 - 1 of B^T from the same
+// shared-memory offsets, and receives its 128 rows of D in its own TMEM at the same address; the
+// allocation is collective (both CTAs allocate and obtain the same address).
+OZ_DEVICE_INLINE uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+OZ_DEVICE_INLINE uint32_t cluster_id() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+OZ_DEVICE_INLINE void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// shared::cluster address of the same shared-memory offset in CTA `rank` of the cluster
+OZ_DEVICE_INLINE uint32_t mapa_shared(uint32_t a, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+// arrive on an mbarrier of another CTA of the cluster (shared::cluster address)
+OZ_DEVICE_INLINE void mbar_arrive_remote(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+OZ_DEVICE_INLINE void tmem_alloc_pair(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+OZ_DEVICE_INLINE void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// completion of the issuing thread's earlier pair MMAs, signalled on the mbarrier at this offset in
+// both CTAs of the pair
+OZ_DEVICE_INLINE void tc_commit_pair(uint32_t mbar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(mbar),
+      "h"((uint16_t)3)
+      : "memory");
+}
+template <int COL>
+OZ_DEVICE_INLINE void mma_f16_pair(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  if constexpr (COL == 0)
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+  else if constexpr (COL == 1)
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::2.kind::f16.collector::a::fill [%0], %1, %2, "
+        "%3, p;\n}" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+  else if constexpr (COL == 2)
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::2.kind::f16.collector::a::use [%0], %1, %2, "
+        "%3, p;\n}" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+  else
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::2.kind::f16.collector::a::lastuse [%0], %1, "
+        "%2, %3, p;\n}" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
 // 32 lanes x 32 columns of 32-bit TMEM words: thread i of the warp gets lane (base+i), 32 columns.
 OZ_DEVICE_INLINE void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(

@@ -19,6 +19,15 @@
 //                q * 256^(s-1-g) into exact running sums per output element, then rounds once to
 //                FP64 scaled by 2^(ea+eb-8s-6), applies alpha/beta, stores (and for the row-table
 //                mode records a per-row |max| for the next slicing).
+// CTA pairs (gemm_kernel<true>, clusters of two CTAs on two SMs): one tile is 256 x 64; each CTA
+// loads its own 128 A rows and one 32-row half of the 64 B^T rows (the operand stores the halves of
+// each k-block apart), the first CTA's thread issues cta_group::2 MMAs of M = 256 for both (each CTA
+// accumulates its 128 rows in its own TMEM), commits signal the barriers of both CTAs, the second
+// CTA's warp 1 forwards its operand arrivals to the first CTA's stage barriers, and both epilogues
+// release drained buffers on the first CTA's barriers.  One issuing thread then drives two SMs.
+// Measured on GB300 it is not faster: a pair instruction takes about as long in the running kernel
+// as two single-CTA ones on two SMs, and each drain waits for the slower of two epilogues, so the
+// single-CTA tiles stay the default.
 // The drain schedule: diagonal g takes p = 16(g+1) products per k-block; its groups hold
 // floor(GROUP_TERMS/p) k-blocks (the first group of long tiles is shortened per diagonal so that the
 // drains of different diagonals do not coincide).  The first k-block of a tile is issued diagonal by
@@ -36,6 +45,8 @@ namespace oz {
 constexpr int A_TILE_BYTES = TILE_M * KB * 2;             // 4 KB per plane
 constexpr int B_TILE_BYTES = BN * KB * 2;                 // 2 KB per plane
 constexpr int PLANE_BYTES = A_TILE_BYTES + B_TILE_BYTES;  // one slice plane of A and of B^T per k-block
+constexpr int BH_BYTES = B_TILE_BYTES / 2;                // a CTA pair: each CTA's half (32 rows) of a B^T plane
+__host__ __device__ constexpr int plane_bytes(bool pair) { return A_TILE_BYTES + (pair ? BH_BYTES : B_TILE_BYTES); }
 constexpr int EPI_WARPS = 16;
 constexpr int CW = BN / (EPI_WARPS / 4);                  // columns per epilogue warp (16)
 constexpr int NTHREADS = 32 * (2 + EPI_WARPS);
@@ -54,13 +65,13 @@ struct Shared {
 };
 
 // pipeline stages that fit next to the staging area for slice level smax
-int gemm_stages(int smax) {
+int gemm_stages(int smax, bool pair) {
   const int avail = SMEM_LIMIT - ZS_BYTES - (int)sizeof(Shared) - 1024;
-  const int n = avail / (smax * PLANE_BYTES);
+  const int n = avail / (smax * plane_bytes(pair));
   return n < MAX_STAGES ? n : MAX_STAGES;
 }
-size_t gemm_smem_bytes(int smax) {
-  return (size_t)gemm_stages(smax) * smax * PLANE_BYTES + ZS_BYTES + sizeof(Shared) + 1024;
+size_t gemm_smem_bytes(int smax, bool pair) {
+  return (size_t)gemm_stages(smax, pair) * smax * plane_bytes(pair) + ZS_BYTES + sizeof(Shared) + 1024;
 }
 
 __device__ __forceinline__ uint32_t bar(const unsigned long long* p) { return smem_u32(p); }
@@ -118,15 +129,29 @@ __device__ __forceinline__ uint32_t acquire(Shared& sh, MmaCtl& c, volatile int*
   }
   return b;
 }
+template <bool PAIR>
+__device__ __forceinline__ void commit_to(uint32_t mbar) {
+  if constexpr (PAIR) tc_commit_pair(mbar);
+  else tc_commit(mbar);
+}
+template <bool PAIR, int COL>
+__device__ __forceinline__ void mma_issue(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  if constexpr (PAIR) mma_f16_pair<COL>(d, a, b, id, acc);
+  else mma_f16<COL>(d, a, b, id, acc);
+}
+template <bool PAIR>
 __device__ __forceinline__ void post(Shared& sh, MmaCtl& c, uint32_t b) {
-  tc_commit(bar(&sh.accf[b]));
+  commit_to<PAIR>(bar(&sh.accf[b]));
   c.r.posted(b);
 }
 
-template <int S>
+// The MMAs of one tile: PAIR = one instruction of M = 256 over the CTA pair (issued by the first
+// CTA; each CTA holds its own A rows and half of the B^T rows at the same shared-memory offsets).
+template <int S, bool PAIR>
 __device__ void mma_tile(Shared& sh, MmaCtl& c, uint32_t tmem, uint32_t stage0, uint32_t stage_bytes, uint32_t boff,
                          int nkb, volatile int* abort) {
-  constexpr uint32_t IDESC = idesc_f16(TILE_M, BN);
+  constexpr uint32_t IDESC = idesc_f16(PAIR ? 2 * TILE_M : TILE_M, BN);
+  constexpr int BPL = PAIR ? BH_BYTES : B_TILE_BYTES;  // bytes between the B^T planes of a stage
   uint32_t buf[S];
   int nxt[S], per[S];
   const bool stag = stagger_of(nkb);
@@ -148,10 +173,10 @@ __device__ void mma_tile(Shared& sh, MmaCtl& c, uint32_t tmem, uint32_t stage0, 
       const uint32_t d = tmem + buf[g] * BN;
 #pragma unroll
       for (int t = 0; t <= g; ++t)
-        mma_f16<0>(d, ad0 + (uint64_t)((t * A_TILE_BYTES) >> 4), bd0 + (uint64_t)(((g - t) * B_TILE_BYTES) >> 4), IDESC,
-                   t > 0 ? 1u : 0u);
+        mma_issue<PAIR, 0>(d, ad0 + (uint64_t)((t * A_TILE_BYTES) >> 4), bd0 + (uint64_t)(((g - t) * BPL) >> 4), IDESC,
+                           t > 0 ? 1u : 0u);
     }
-    tc_commit(bar(&sh.empty[c.rg.stg]));
+    commit_to<PAIR>(bar(&sh.empty[c.rg.stg]));
     c.rg.advance();
   }
   uint32_t fresh = 0u;  // diagonals whose current buffer has not been written yet
@@ -161,7 +186,7 @@ __device__ void mma_tile(Shared& sh, MmaCtl& c, uint32_t tmem, uint32_t stage0, 
 #pragma unroll
       for (int g = 0; g < S; ++g) {
         if (nxt[g] == kb) {
-          post(sh, c, buf[g]);
+          post<PAIR>(sh, c, buf[g]);
           buf[g] = acquire(sh, c, abort);
           fresh |= 1u << g;
           nxt[g] += per[g];
@@ -179,31 +204,32 @@ __device__ void mma_tile(Shared& sh, MmaCtl& c, uint32_t tmem, uint32_t stage0, 
 #pragma unroll
       for (int u = 0; u < S - t; ++u) {
         const int g = t + u;
-        const uint64_t bd = bd0 + (uint64_t)((u * B_TILE_BYTES) >> 4);
+        const uint64_t bd = bd0 + (uint64_t)((u * BPL) >> 4);
         const uint32_t d = tmem + buf[g] * BN;
         // the first product of a k-block into diagonal g is the one with t = 0
         const uint32_t acc = (t == 0) ? (((fresh >> g) & 1u) ^ 1u) : 1u;
         const int nu = S - t;
-        if (nu == 1) mma_f16<0>(d, ad, bd, IDESC, acc);
-        else if (u == 0) mma_f16<1>(d, ad, bd, IDESC, acc);
-        else if (u == nu - 1) mma_f16<3>(d, ad, bd, IDESC, acc);
-        else mma_f16<2>(d, ad, bd, IDESC, acc);
+        if (nu == 1) mma_issue<PAIR, 0>(d, ad, bd, IDESC, acc);
+        else if (u == 0) mma_issue<PAIR, 1>(d, ad, bd, IDESC, acc);
+        else if (u == nu - 1) mma_issue<PAIR, 3>(d, ad, bd, IDESC, acc);
+        else mma_issue<PAIR, 2>(d, ad, bd, IDESC, acc);
       }
     }
     fresh = 0u;
-    tc_commit(bar(&sh.empty[c.rg.stg]));
+    commit_to<PAIR>(bar(&sh.empty[c.rg.stg]));
     c.rg.advance();
   }
 #pragma unroll
-  for (int g = 0; g < S; ++g) post(sh, c, buf[g]);
+  for (int g = 0; g < S; ++g) post<PAIR>(sh, c, buf[g]);
 }
 
 // Epilogue side of one drain: wait until the MMAs into buffer b are complete, read this warp's
 // 32 x CW slice, release the buffer, add q * 2^shl into the exact running sums (one 96-bit
 // two's-complement integer w2:w1:w0 per output element).
+// (In a CTA pair the buffer is released on the first CTA's barrier, where the issuer waits for it.)
 __device__ __forceinline__ bool drain_into(Shared& sh, uint32_t tmem, int lq, int cg, int lane, uint32_t b, int shl,
                                            uint32_t& accf_par, volatile int* abort, uint32_t (&z0)[CW],
-                                           uint32_t (&z1)[CW], uint32_t (&z2)[CW]) {
+                                           uint32_t (&z1)[CW], uint32_t (&z2)[CW], bool remote_release) {
   if (!mbar_wait(bar(&sh.accf[b]), (accf_par >> b) & 1u, abort)) return false;
   accf_par ^= 1u << b;
   tc_fence_after();
@@ -212,7 +238,10 @@ __device__ __forceinline__ bool drain_into(Shared& sh, uint32_t tmem, int lq, in
   tmem_wait_ld();
   tc_fence_before();
   __syncwarp();
-  if (lane == 0) mbar_arrive(bar(&sh.acce[b]));
+  if (lane == 0) {
+    if (remote_release) mbar_arrive_remote(mapa_shared(bar(&sh.acce[b]), 0));
+    else mbar_arrive(bar(&sh.acce[b]));
+  }
 #pragma unroll
   for (int j = 0; j < CW; ++j) w96_add_shifted(z0[j], z1[j], z2[j], __float2int_rn(__uint_as_float(v[j])), shl);
   return true;
@@ -233,42 +262,54 @@ __device__ __forceinline__ void tile_of(const GemmTile* tiles, const GemmProblem
   }
 }
 
+template <bool PAIR>
 __global__ void __launch_bounds__(NTHREADS, 1)
     gemm_kernel(const GemmProblem* __restrict__ probs, const GemmTile* __restrict__ tiles, int ntiles,
                 const int* __restrict__ first,
                 const __grid_constant__ GemmProblem single, int smax, int nstage, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const uint32_t stage_bytes = (uint32_t)(smax * PLANE_BYTES), boff = (uint32_t)(smax * A_TILE_BYTES);
+  constexpr int BPL = PAIR ? BH_BYTES : B_TILE_BYTES;  // bytes of one B^T plane in a stage
+  const uint32_t stage_bytes = (uint32_t)(smax * plane_bytes(PAIR)), boff = (uint32_t)(smax * A_TILE_BYTES);
   longlong2* zstage = reinterpret_cast<longlong2*>(smem + nstage * stage_bytes);
   Shared& sh = *reinterpret_cast<Shared*>(smem + nstage * stage_bytes + ZS_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* abort = &sh.abort;
   const uint32_t stage0 = smem_u32(smem);
+  // CTA pair: rank 0 issues the MMAs of both; rank 1 forwards its operand arrivals to rank 0
+  const uint32_t rank = PAIR ? cluster_rank() : 0u;
+  const bool lead = rank == 0;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < nstage; ++i) {
-      mbar_init(bar(&sh.full[i]), 1);
+      // the first CTA of a pair also waits for the second one's copies (one forwarded arrival)
+      mbar_init(bar(&sh.full[i]), PAIR && lead ? 2 : 1);
       mbar_init(bar(&sh.empty[i]), 1);
     }
     for (int i = 0; i < NBUF; ++i) {
       mbar_init(bar(&sh.accf[i]), 1);
-      mbar_init(bar(&sh.acce[i]), EPI_WARPS);
+      mbar_init(bar(&sh.acce[i]), PAIR ? 2 * EPI_WARPS : EPI_WARPS);
     }
     mbar_init(bar(&sh.fin), 1);
     sh.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) tmem_alloc(smem_u32(&sh.tmem), 512);
+  if (warp == 1) {
+    if constexpr (PAIR) tmem_alloc_pair(smem_u32(&sh.tmem), 512);
+    else tmem_alloc(smem_u32(&sh.tmem), 512);
+  }
   tc_fence_before();
-  __syncthreads();
+  if constexpr (PAIR) cluster_sync();
+  else __syncthreads();
   tc_fence_after();
   const uint32_t tmem = sh.tmem;
-  // this CTA's tiles: the range [first[b], first[b+1]) of a host-balanced list, or every
-  // gridDim.x-th tile; all three roles walk the same sequence
-  const int it0 = first ? first[blockIdx.x] : (int)blockIdx.x;
-  const int it1 = first ? first[blockIdx.x + 1] : ntiles;
-  const int istep = first ? 1 : (int)gridDim.x;
+  // this CTA's (pair's) tiles: the range [first[b], first[b+1]) of a host-balanced list, or every
+  // grid-th tile; all roles (of both CTAs of a pair) walk the same sequence
+  const int unit = PAIR ? (int)cluster_id() : (int)blockIdx.x;
+  const int units = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+  const int it0 = first ? first[unit] : unit;
+  const int it1 = first ? first[unit + 1] : ntiles;
+  const int istep = first ? 1 : units;
 
   if (warp == 0) {
     // ------------------------------------------------------------------ producer
@@ -280,8 +321,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         int mb, nb;
         tile_of(tiles, probs, single, idx, P, mb, nb);
         const int nkb = P->nkb, s = P->s, SA = P->SA, SB = P->SB;
-        const char* Ab = reinterpret_cast<const char*>(P->A) + (long long)mb * nkb * SA * A_TILE_BYTES;
-        const char* Bb = reinterpret_cast<const char*>(P->B) + (long long)nb * nkb * SB * B_TILE_BYTES;
+        // a pair's tile is 256 rows: this CTA's A tile is 2 mb + rank; its B^T half is the rank-th
+        // 32-row half of the 64-row tile nb (the operand stores the two halves of each k-block apart).
+        // An operand with an odd number of 128-row tiles has no A tile for the second CTA of its last
+        // pair: that CTA loads only its B^T half, and the rows it computes lie beyond M (never stored).
+        const int ma = PAIR ? 2 * mb + (int)rank : mb;
+        const bool a_in = !PAIR || ma * TILE_M < P->M;
+        const char* Ab = reinterpret_cast<const char*>(P->A) + (long long)ma * nkb * SA * A_TILE_BYTES;
+        const char* Bb = reinterpret_cast<const char*>(P->B) + (long long)nb * nkb * SB * B_TILE_BYTES +
+                         (PAIR ? (long long)rank * SB * BH_BYTES : 0ll);
         bool stop = false;
         for (int kb = 0; kb < nkb; ++kb) {
           // a stage is refilled once the MMAs of its previous fill have completed
@@ -289,11 +337,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             stop = true;
             break;
           }
-          mbar_expect_tx(bar(&sh.full[rg.stg]), (uint32_t)(s * PLANE_BYTES));
+          mbar_expect_tx(bar(&sh.full[rg.stg]), (uint32_t)(s * ((a_in ? A_TILE_BYTES : 0) + BPL)));
           const uint32_t dA = stage0 + rg.stg * stage_bytes;
-          bulk_g2s(dA, Ab + (long long)kb * SA * A_TILE_BYTES, (uint32_t)(s * A_TILE_BYTES), bar(&sh.full[rg.stg]));
-          bulk_g2s(dA + boff, Bb + (long long)kb * SB * B_TILE_BYTES, (uint32_t)(s * B_TILE_BYTES),
-                   bar(&sh.full[rg.stg]));
+          if (a_in)
+            bulk_g2s(dA, Ab + (long long)kb * SA * A_TILE_BYTES, (uint32_t)(s * A_TILE_BYTES), bar(&sh.full[rg.stg]));
+          bulk_g2s(dA + boff, Bb + (long long)kb * SB * B_TILE_BYTES, (uint32_t)(s * BPL), bar(&sh.full[rg.stg]));
           ++fills;
           rg.advance();
         }
@@ -309,8 +357,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
     }
   } else if (warp == 1) {
-    // ------------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
+    if (lane == 0 && lead) {
+      // ------------------------------------------------------------------ MMA issuer
       MmaCtl c{Ring{0, 0, nstage}, BufRing{0u, 0, 0}, 0u};
       for (int idx = it0; idx < it1 && !*abort; idx += istep) {
         const GemmProblem* P;
@@ -318,21 +366,41 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         tile_of(tiles, probs, single, idx, P, mb, nb);
         const int nkb = P->nkb;
         switch (P->s) {
-          case 1: mma_tile<1>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
-          case 2: mma_tile<2>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
-          case 3: mma_tile<3>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
-          case 4: mma_tile<4>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
-          case 5: mma_tile<5>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
-          case 6: mma_tile<6>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
-          case 7: mma_tile<7>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
-          case 8: mma_tile<8>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
+          case 1: mma_tile<1, PAIR>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
+          case 2: mma_tile<2, PAIR>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
+          case 3: mma_tile<3, PAIR>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
+          case 4: mma_tile<4, PAIR>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
+          case 5: mma_tile<5, PAIR>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
+          case 6: mma_tile<6, PAIR>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
+          case 7: mma_tile<7, PAIR>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
+          case 8: mma_tile<8, PAIR>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
           default: *abort = 1; break;
         }
       }
       // all issued MMAs complete before TMEM is released
-      tc_commit(bar(&sh.fin));
+      commit_to<PAIR>(bar(&sh.fin));
       volatile int never = 0;
       mbar_wait(bar(&sh.fin), 0, &never);
+    } else if (PAIR && lane == 0) {
+      // ------------------------------------------------------------------ forwarder (second CTA)
+      // every fill of this CTA's stage ring, once its copies have landed, counts as one arrival on
+      // the first CTA's barrier of the same stage, which its issuer waits on
+      Ring rg{0, 0, nstage};
+      for (int idx = it0; idx < it1 && !*abort; idx += istep) {
+        const GemmProblem* P;
+        int mb, nb;
+        tile_of(tiles, probs, single, idx, P, mb, nb);
+        bool stop = false;
+        for (int kb = 0; kb < P->nkb; ++kb) {
+          if (!mbar_wait(bar(&sh.full[rg.stg]), (uint32_t)rg.ph, abort)) {
+            stop = true;
+            break;
+          }
+          mbar_arrive_remote(mapa_shared(bar(&sh.full[rg.stg]), 0));
+          rg.advance();
+        }
+        if (stop) break;
+      }
     }
   } else {
     // ------------------------------------------------------------------ epilogue
@@ -347,7 +415,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       tile_of(tiles, probs, single, idx, P, mb, nb);
       // per-tile operands of the final stage, loaded now so that their latency hides behind the drains
       const int M = P->M, N = P->N, mode = P->mode;
-      const int row = mb * TILE_M + lq * 32 + lane;
+      const int row = (PAIR ? 2 * mb + (int)rank : mb) * TILE_M + lq * 32 + lane;
       const bool rowok = row < M;
       const int col0 = nb * BN + cg * CW;
       const int ebl = (lane < CW && col0 + lane < N) ? __ldg(P->eb + col0 + lane) : 0;
@@ -386,13 +454,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             gsel = g;
           }
         if (gsel < 0) break;
-        ok = drain_into(sh, tmem, lq, cg, lane, bufs[gsel], 8 * (S - 1 - gsel), accf_par, abort, z0, z1, z2);
+        ok = drain_into(sh, tmem, lq, cg, lane, bufs[gsel], 8 * (S - 1 - gsel), accf_par, abort, z0, z1, z2,
+                        PAIR && !lead);
         er.posted(bufs[gsel]);
         bufs[gsel] = er.next();
         nxt[gsel] += per[gsel];
       }
       for (int g = 0; g < S && ok; ++g) {
-        ok = drain_into(sh, tmem, lq, cg, lane, bufs[g], 8 * (S - 1 - g), accf_par, abort, z0, z1, z2);
+        ok = drain_into(sh, tmem, lq, cg, lane, bufs[g], 8 * (S - 1 - g), accf_par, abort, z0, z1, z2, PAIR && !lead);
         er.posted(bufs[g]);
       }
       if (!ok) break;
@@ -447,10 +516,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 
   tc_fence_before();
-  __syncthreads();
+  if constexpr (PAIR) cluster_sync();  // both CTAs' epilogues are done with TMEM, remote arrivals are in
+  else __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, 512);
+    if constexpr (PAIR) tmem_dealloc_pair(tmem, 512);
+    else tmem_dealloc(tmem, 512);
   }
   if (threadIdx.x == 0 && sh.abort) atomicOr(err, 2);
 }
@@ -512,33 +583,81 @@ void balance_tiles(const std::vector<GemmProblem>& probs, std::vector<GemmTile>&
   tiles.swap(out);
 }
 
-cudaError_t launch_gemm(const GemmProblem* d_probs, const GemmTile* d_tiles, int ntiles, int grid,
-                        const GemmProblem* single, int smax, int* d_err, cudaStream_t st, const int* d_first) {
-  if (ntiles <= 0) return cudaSuccess;
-  // The shared-memory opt-in belongs to the current device's context: record it per device
-  // ordinal (bit d of a process-wide mask).  Setting it twice is harmless, so two host threads
-  // racing on the same device need no lock.
+namespace {
+// The shared-memory opt-in of a kernel belongs to the current device's context: record it per
+// device ordinal (bit d of a process-wide mask).  Setting it twice is harmless, so two host threads
+// racing on the same device need no lock.
+template <bool PAIR>
+cudaError_t opt_in_smem() {
   static std::atomic<unsigned long long> attr_set{0ull};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
   if (!bit || !(attr_set.load(std::memory_order_acquire) & bit)) {
-    e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
+    e = cudaFuncSetAttribute(gemm_kernel<PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
     if (e != cudaSuccess) return e;
     attr_set.fetch_or(bit, std::memory_order_release);
   }
+  return cudaSuccess;
+}
+}  // namespace
+
+int gemm_pair_units(int nsm) {
+  // CTA pairs that run at the same time on the current device (clusters of 2, one CTA per SM)
+  if (opt_in_smem<true>() != cudaSuccess) return 0;
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)(nsm / 2 * 2), 1, 1);
+  cfg.blockDim = dim3(NTHREADS, 1, 1);
+  cfg.dynamicSmemBytes = gemm_smem_bytes(MAX_LEVEL, true);
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, gemm_kernel<true>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n < nsm / 2 ? n : nsm / 2;
+}
+
+cudaError_t launch_gemm(const GemmProblem* d_probs, const GemmTile* d_tiles, int ntiles, int grid,
+                        const GemmProblem* single, int smax, int* d_err, cudaStream_t st, const int* d_first,
+                        bool pair) {
+  if (ntiles <= 0) return cudaSuccess;
+  cudaError_t e = pair ? opt_in_smem<true>() : opt_in_smem<false>();
+  if (e != cudaSuccess) return e;
   GemmProblem one{};
   if (single) {
     one = *single;
     smax = one.s;
   }
   if (smax < 1 || smax > MAX_LEVEL) return cudaErrorInvalidValue;
-  const int nstage = gemm_stages(smax);
+  const int nstage = gemm_stages(smax, pair);
   const int g = d_first ? grid : (grid < ntiles ? grid : ntiles);
-  gemm_kernel<<<g, NTHREADS, gemm_smem_bytes(smax), st>>>(d_probs, d_tiles, ntiles, d_first, one, smax, nstage,
-                                                          d_err);
-  return cudaGetLastError();
+  if (!pair) {
+    gemm_kernel<false><<<g, NTHREADS, gemm_smem_bytes(smax, false), st>>>(d_probs, d_tiles, ntiles, d_first, one, smax,
+                                                                         nstage, d_err);
+    return cudaGetLastError();
+  }
+  // g CTA pairs: clusters of two CTAs on two SMs
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)(2 * g), 1, 1);
+  cfg.blockDim = dim3(NTHREADS, 1, 1);
+  cfg.dynamicSmemBytes = gemm_smem_bytes(smax, true);
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, gemm_kernel<true>, d_probs, d_tiles, ntiles, d_first, one, smax, nstage, d_err);
 }
 
 }  // namespace oz

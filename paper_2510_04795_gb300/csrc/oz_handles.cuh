@@ -96,6 +96,8 @@ struct oz_heff_s {
   std::vector<oz::GemmTile> ht1, ht2;  // the same, scheduled over the CTAs (uploaded)
   int *dF1 = nullptr, *dF2 = nullptr;  // per-CTA first tile of each stage (nsm + 1 entries)
   int sched1 = 0, sched2 = 0;          // schedule of each stage (oz::SCHED_*), set by the autotuner
+  bool pair = false;                   // products on CTA pairs (256 x 64 tiles)
+  int units = 0;                       // persistent units of the GEMM launches: CTAs, or CTA pairs
   int balance();                       // (re)assigns the tiles to CTAs for the current levels
   std::vector<int> p1sec, p2sec;
   std::vector<int> lev1, lev2;  // per source sector (stage 1), per target sector (stage 2)

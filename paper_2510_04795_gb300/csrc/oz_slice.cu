@@ -185,7 +185,17 @@ __global__ void __launch_bounds__(256) digits_kernel(const SliceSeg* __restrict_
   }
   int K = g.k0 + c * 8;
   int rt = R / g.TR, rr = R % g.TR, kb = K >> KB_SHIFT, kk = K & (KB - 1);
-  long long base = (((long long)rt * g.nkb + kb) * g.S) * (long long)(g.TR * KB) + tile_off(rr, kk);
+  // plane t of (row, k) at base + t * pstride; a half-major operand stores the 32-row halves of each
+  // k-block of a tile one after the other (each half: S planes of 32 rows)
+  long long base;
+  int pstride;
+  if (g.half_major) {
+    base = ((((long long)rt * g.nkb + kb) * 2 + (rr >> 5)) * g.S) * (long long)(32 * KB) + tile_off(rr & 31, kk);
+    pstride = 32 * KB;
+  } else {
+    base = (((long long)rt * g.nkb + kb) * g.S) * (long long)(g.TR * KB) + tile_off(rr, kk);
+    pstride = g.TR * KB;
+  }
   if constexpr (S <= 8) {
     // Balanced base-256 digits by one add: with Y = X + sum_t 128 * 256^t (0 <= Y < 256^S because
     // the exponent rule keeps |X| <= 127 * 256^(S-1)), byte t of Y is d + 128 for the digit of
@@ -215,7 +225,7 @@ __global__ void __launch_bounds__(256) digits_kernel(const SliceSeg* __restrict_
         h = __hsub2(h, off);
         op[p] = *reinterpret_cast<uint32_t*>(&h);
       }
-      *reinterpret_cast<uint4*>(g.dst + base + (long long)t * (g.TR * KB)) = o;
+      *reinterpret_cast<uint4*>(g.dst + base + (long long)t * pstride) = o;
     }
   } else {
     // S = 9: the fixed-point value needs more than 64 bits
@@ -244,7 +254,7 @@ __global__ void __launch_bounds__(256) digits_kernel(const SliceSeg* __restrict_
       w.y = *reinterpret_cast<uint32_t*>(&h1);
       w.z = *reinterpret_cast<uint32_t*>(&h2);
       w.w = *reinterpret_cast<uint32_t*>(&h3);
-      *reinterpret_cast<uint4*>(g.dst + base + (long long)t * (g.TR * KB)) = w;
+      *reinterpret_cast<uint4*>(g.dst + base + (long long)t * pstride) = w;
     }
   }
 }

@@ -28,6 +28,8 @@ struct SliceSeg {
   int* rowexp;                 // per operand row: shared exponent (written by the digit pass)
   long long unit0;             // first digit-pass work unit of this segment (prefix over segments)
   long long unit0m;            // first rowmax-pass work unit of this segment
+  int half_major;              // TR = 64 only: the two 32-row halves of each k-block stored apart
+                               // ([tile][k-block][half][plane][32 x 16]), for CTA-pair products
 };
 
 // Up to 4 segments passed by value (no host-to-device copy for single products).

@@ -28,12 +28,16 @@ def _tasks(st, blocks):
     return [(int(s), int(d), float(st.term_coef[k]), L, R) for (k, s, d), (L, R) in zip(st.tasks, blocks)]
 
 
+@pytest.mark.parametrize("tile", ["cta", "pair"])
 @pytest.mark.parametrize("seed,grid,dims,S,s", [(1, (3, 3), (2, 20), 7, 7), (2, (4, 3), (5, 70), 4, 4),
-                                               (3, (3, 2), (60, 140), 9, 6)])
-def test_heff_bitexact_vs_emulated_oracle(ctx, seed, grid, dims, S, s):
+                                               (3, (3, 2), (60, 140), 9, 6), (4, (4, 4), (30, 300), 7, 7)])
+def test_heff_bitexact_vs_emulated_oracle(ctx, seed, grid, dims, S, s, tile):
+    """Both tilings of the products (128 x 64 on one CTA; 256 x 64 on a CTA pair, with the pair's
+    padding tile of odd operands and both stage-2 orientations) give the oracle's bits."""
     import paper_2510_04795_gb300 as oz
     st, blocks, psi = _problem(grid, dims, 8, True, seed)
-    h = oz.Heff(ctx, st.m, st.n, _tasks(st, blocks), slices=S, level=s)
+    h = oz.Heff(ctx, st.m, st.n, _tasks(st, blocks), slices=S, level=s, tile=tile)
+    assert h.info()["tile"] == (1 if tile == "cta" else 2)
     y = h.apply(psi)
     ctx.status()
     Lb = [b[0].cpu().numpy() for b in blocks]
