@@ -316,8 +316,8 @@ def train_learned_selector(ctx, args):
 def slice_sweep(ctx):
     """The precision dial on the 40-block workload (sizes 8-256, entries N(0,1) 2^-j with j up to 19:
     about six decades of exponent spread inside every block, 128 terms): H_eff psi with s slices for
-    s = 3..8 (an S = 9 handle multiplies at level 8, so s = 9 is not a separate row), its relative
-    Frobenius error against the FP64 oracle (per-block numpy products on the host) and its throughput."""
+    s = 3..9 (level 9 runs each tile in two passes), its relative Frobenius error against the FP64
+    oracle (per-block numpy products on the host) and its throughput."""
     import numpy as np
     import torch
     import synthetic
@@ -332,7 +332,7 @@ def slice_sweep(ctx):
              for (k, sr, d), (L, R) in zip(st.tasks, blocks)]
     psi = psi_h.cuda()
     rows = []
-    for s in range(3, 9):
+    for s in range(3, 10):
         h = oz.Heff(ctx, st.m, st.n, tasks, slices=s)
         y = h.apply(psi)
         for _ in range(3):

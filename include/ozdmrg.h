@@ -57,7 +57,9 @@ extern "C" {
 
 typedef struct oz_prec {
   int slices; /* S: digits stored per value, 1..9 */
-  int level;  /* s: digits used, 1..min(S, 8); 0 means s = S */
+  int level;  /* s: digits used, 1..S; 0 means s = S.  Level 9 runs each tile in two passes (nine
+                 diagonal accumulators exceed TMEM) and accepts reductions k <= 130048, where the
+                 exact 96-bit sums cannot overflow; levels up to 8 accept k <= 1048576 */
   int mode;   /* OZ_MODE_EAGER or OZ_MODE_NATIVE (OZ_MODE_PERFORMANT: ozaki_gemm only) */
   int tile;   /* H_eff handles: OZ_TILE_AUTO (0), OZ_TILE_CTA (128 x 64 tiles, one CTA each) or
                  OZ_TILE_PAIR (256 x 64 tiles on a CTA pair: one MMA issuer for two SMs); AUTO
@@ -97,8 +99,8 @@ int oz_status(oz_ctx* ctx, oz_stream_t stream);
  *   into a scratch C (synchronising the stream, allocating m x n doubles), caches the winner in the
  *   context and then runs it; later calls of the class run the cached choice.  The result is that
  *   of the chosen path (bit-exact emulation or cuBLAS DGEMM).  Not for use under stream capture.
- * Errors: OZ_EINVAL for negative sizes, short leading dimensions, slices outside 1..9 or a level
- * outside 1..min(S,8).  May grow the context workspace (cudaMalloc, synchronous): call it once
+ * Errors: OZ_EINVAL for negative sizes, short leading dimensions, slices outside 1..9, a level
+ * outside 1..S, or k above the level's limit (1048576; 130048 at level 9).  May grow the context workspace (cudaMalloc, synchronous): call it once
  * outside stream capture before capturing.
  * ------------------------------------------------------------------------------------------ */
 int ozaki_gemm(oz_ctx* ctx, int m, int n, int k, double alpha, const double* d_A, int lda, const double* d_B,
@@ -128,7 +130,7 @@ int oz_performant_choice(oz_ctx* ctx, int m, int n, int k, const oz_prec* prec, 
  *   - All calls share the array and it keeps the last call's contents; the parts that must start
  *     at zero are cleared on the stream by each call.  Calls whose execution overlaps on the GPU
  *     (different streams, or concurrent host threads) race on the array: serialise them.
- * Arguments as ozaki_gemm; slices S in 1..9, level in 1..min(S,8) (0 = S).
+ * Arguments as ozaki_gemm; slices S in 1..9, level in 1..S (0 = S).
  * ------------------------------------------------------------------------------------------ */
 int ozaki_gemm_noalloc(int m, int n, int k, double alpha, const double* d_A, int lda, const double* d_B, int ldb,
                        double beta, double* d_C, int ldc, int slices, int level, oz_stream_t stream);
@@ -272,8 +274,9 @@ int oz_reduce_ordered(const double* const* d_parts, int nparts, long long len, d
  *   `budget` is a relative Frobenius error, `margin` a safety in decades).  selector:
  *   OZ_SELECT_FIXED (the handle's level), OZ_SELECT_ANALYTIC (error 2^(gA + gB - 8 s + 3) from
  *   the effective exponent gaps), OZ_SELECT_LEARNED (`net`, OZ_NFEAT inputs, outputs = log10
- *   error at levels 3..8).  Levels below 3 are never picked.  Writes the levels to s1/s2 (may be
- *   null).
+ *   error at levels 3..8).  Levels below 3 are never picked.  A handle at level 9 (the fixed
+ *   fallback) starts there with its error counted as zero and is lowered from 9 to 8 like any
+ *   other step.  Writes the levels to s1/s2 (may be null).
  * ------------------------------------------------------------------------------------------ */
 #define OZ_NFEAT 20
 #define OZ_SELECT_FIXED 0

@@ -37,16 +37,13 @@ int cuda_fail(cudaError_t e, const char* where) {
   } while (0)
 
 inline long long cdiv(long long a, long long b) { return (a + b - 1) / b; }
-// Longest reduction one product accepts: the epilogue's two 64-bit partial sums stay exact while
-// every diagonal has fewer than 2^13 accumulator groups of GROUP_TERMS products.
-constexpr long long OZ_MAX_K = 1ll << 20;
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 int check_prec(const oz_prec* p, int* S, int* s, int* mode) {
   if (!p) return fail(OZ_EINVAL, "prec is null");
   if (p->slices < 1 || p->slices > 9) return fail(OZ_EINVAL, "slices must be in 1..9");
   int lvl = p->level == 0 ? p->slices : p->level;
-  if (lvl < 1 || lvl > p->slices || lvl > oz::MAX_LEVEL) return fail(OZ_EINVAL, "level must be in 1..min(S,8)");
+  if (lvl < 1 || lvl > p->slices || lvl > oz::MAX_LEVEL) return fail(OZ_EINVAL, "level must be in 1..S");
   if (p->mode != OZ_MODE_EAGER && p->mode != OZ_MODE_NATIVE) return fail(OZ_EINVAL, "unknown mode");
   *S = p->slices;
   *s = lvl;
@@ -215,7 +212,7 @@ extern "C" int ozaki_gemm(oz_ctx* c, int m, int n, int k, double alpha, const do
     q.mode = OZ_MODE_EAGER;
     int S, s, md;
     if (int rc = check_prec(&q, &S, &s, &md)) return rc;
-    if (m > 0 && n > 0 && k > 0 && k <= OZ_MAX_K && lda >= k && ldb >= n && ldc >= n) {
+    if (m > 0 && n > 0 && k > 0 && k <= oz::max_k_of_level(s) && lda >= k && ldb >= n && ldc >= n) {
       const unsigned long long key = perf_key(m, n, k, S, s);
       auto it = c->perf.find(key);
       if (it == c->perf.end()) {
@@ -255,7 +252,9 @@ extern "C" int ozaki_gemm(oz_ctx* c, int m, int n, int k, double alpha, const do
   if (m < 0 || n < 0 || k < 0) return fail(OZ_EINVAL, "negative size");
   if (lda < std::max(k, 1) || ldb < std::max(n, 1) || ldc < std::max(n, 1)) return fail(OZ_EINVAL, "leading dimension too small");
   if (m == 0 || n == 0) return OZ_OK;
-  if (k > OZ_MAX_K) return fail(OZ_EINVAL, "k exceeds the exact-accumulation limit (1048576)");
+  if (k > oz::max_k_of_level(s))
+    return fail(OZ_EINVAL, s >= oz::SPLIT_LEVEL ? "k exceeds the exact-accumulation limit of level 9 (130048)"
+                                                : "k exceeds the exact-accumulation limit (1048576)");
   cudaStream_t st = (cudaStream_t)stream;
   if (k == 0) {
     scale_kernel<<<(unsigned)cdiv((long long)m * n, 256), 256, 0, st>>>(C, m, n, ldc, beta);
@@ -441,9 +440,9 @@ int slice_ops(oz_heff_s* h, const oz_task* tasks) {
   const int S = h->S;
   const std::vector<int>& m = h->m;
   const std::vector<int>& n = h->n;
-  std::vector<SliceSeg> ops;
-  ops.reserve(2 * (size_t)h->ntask);
-  long long um = 0, ud = 0;
+  std::vector<SliceSeg> lops, rops;
+  lops.reserve((size_t)h->ntask);
+  rops.reserve((size_t)h->ntask);
   for (int q = 0; q < h->nsec; ++q)
     for (int t : h->bysrc[q]) {
       const oz_task& tk = tasks[t];
@@ -452,10 +451,7 @@ int slice_ops(oz_heff_s* h, const oz_task* tasks) {
       g.r0 = (int)h->rowin1[t]; g.k0 = 0; g.trans = 0; g.S = S; g.scale = 1.0;
       g.dst = h->dA1 + h->A1off[q]; g.TR = oz::TILE_M; g.nkb = h->nkb1[q];
       g.rowmax = h->mA1 + h->A1row[q]; g.rowexp = h->eA1 + h->A1row[q];
-      g.unit0 = ud; g.unit0m = um;
-      ud += oz::digit_units(g.prows, g.pcols);
-      um += oz::rowmax_units(g.rows, g.cols, g.trans);
-      ops.push_back(g);
+      lops.push_back(g);
     }
   for (int q = 0; q < h->nsec; ++q)
     for (int t : h->bydst[q]) {
@@ -466,11 +462,30 @@ int slice_ops(oz_heff_s* h, const oz_task* tasks) {
       g.dst = h->dB2 + h->B2off[q]; g.TR = h->swap2[q] ? oz::TILE_M : oz::BN; g.nkb = h->nkb2[q];
       g.half_major = h->pair && !h->swap2[q] ? 1 : 0;
       g.rowmax = h->mB2 + h->B2row[q]; g.rowexp = h->eB2 + h->B2row[q];
-      g.unit0 = ud; g.unit0m = um;
-      ud += oz::digit_units(g.prows, g.pcols);
-      um += oz::rowmax_units(g.rows, g.cols, g.trans);
+      rops.push_back(g);
+    }
+  // The c*R segments take one FP64 multiply per element, which the FP64 pipe executes far below the
+  // memory rate; the L segments are pure streaming.  Merging the two lists by element count keeps
+  // both kinds in every wave of CTAs, so the multiplies overlap the L segments' memory traffic.
+  std::vector<SliceSeg> ops;
+  ops.reserve(lops.size() + rops.size());
+  {
+    size_t il = 0, ir = 0;
+    long long el = 0, er = 0;
+    while (il < lops.size() || ir < rops.size()) {
+      const bool takel = ir == rops.size() || (il < lops.size() && el <= er);
+      SliceSeg& g = takel ? lops[il++] : rops[ir++];
+      (takel ? el : er) += (long long)g.rows * g.cols;
       ops.push_back(g);
     }
+  }
+  long long um = 0, ud = 0;
+  for (SliceSeg& g : ops) {
+    g.unit0 = ud;
+    g.unit0m = um;
+    ud += oz::digit_units(g.prows, g.pcols);
+    um += oz::rowmax_units(g.rows, g.cols, g.trans);
+  }
   if (ops.empty()) return OZ_OK;
   oz_ctx* c = h->ctx;
   OZ_CU(cudaMemset(h->mA1, 0, (size_t)h->A1row[h->nsec] * 8));
@@ -574,6 +589,8 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
     oz_heff_destroy(h);
     return rc;
   };
+  // longest reduction of one emulated product at this level (native products: the common limit)
+  const long long kmax = mode == OZ_MODE_EAGER ? oz::max_k_of_level(s) : oz::MAX_K;
   if (int rc = h->alloc(&h->dDiag, (size_t)h->dim * 8)) return bail(rc);
   if (int rc = oz::build_heff_diag(nsec, m, n, h->psioff.data(), ntask, tasks, h->dDiag)) return bail(rc);
 
@@ -595,13 +612,17 @@ extern "C" int oz_heff_create(oz_ctx* c, int nsec, const int* m, const int* n, i
       rowin1[t] = rows1[q];
       rows1[q] += m[tasks[t].dst];
     }
+    if (m[q] > kmax) return bail(fail(OZ_EINVAL, "a sector dimension exceeds the level-9 reduction limit (130048)"));
     nkb1[q] = (int)cdiv(m[q], oz::KB);
     long long k2 = 0;
     for (int t : bydst[q]) {
       offk[t] = k2;
       k2 += cdiv(n[tasks[t].src], 8) * 8;
     }
-    if (k2 > OZ_MAX_K) return bail(fail(OZ_EINVAL, "a target sector's concatenated reduction exceeds 1048576"));
+    if (k2 > kmax)
+      return bail(fail(OZ_EINVAL, kmax < oz::MAX_K
+                                      ? "a target sector's concatenated reduction exceeds 130048, the level-9 limit"
+                                      : "a target sector's concatenated reduction exceeds 1048576"));
     nkb2[q] = (int)cdiv(std::max(k2, 1ll), oz::KB);
     ld2[q] = nkb2[q] * oz::KB;
   }
@@ -1127,7 +1148,7 @@ int emulated_batch(oz_ctx* c, const std::vector<EmuJob>& jobs, int S, int s, cud
   std::vector<long long> offA, offB, rowA, rowB;
   long long dA = 0, dB = 0, rA = 0, rB = 0;
   for (const EmuJob& j : jobs) {
-    if (j.M <= 0 || j.N <= 0 || j.K <= 0 || j.K > OZ_MAX_K) return fail(OZ_EINVAL, "emulated batch: bad sizes");
+    if (j.M <= 0 || j.N <= 0 || j.K <= 0 || j.K > oz::max_k_of_level(s)) return fail(OZ_EINVAL, "emulated batch: bad sizes");
     const long long nkb = cdiv(j.K, KB), nrbA = cdiv(j.M, TILE_M), nrbB = cdiv(j.N, BN);
     offA.push_back(dA);
     offB.push_back(dB);

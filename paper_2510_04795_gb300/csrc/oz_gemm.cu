@@ -223,6 +223,43 @@ __device__ void mma_tile(Shared& sh, MmaCtl& c, uint32_t tmem, uint32_t stage0, 
   for (int g = 0; g < S; ++g) post<PAIR>(sh, c, buf[g]);
 }
 
+// Second pass of a level-9 tile: diagonal 8 alone (pairs t + u = 8, t = 0..8) into one buffer at a
+// time; a group holds GROUP_TERMS / 144 = 7 k-blocks, so the buffer is handed to the epilogue at
+// k-blocks 7, 14, ... and at the end of the tile.
+constexpr int LAST_DIAG = SPLIT_LEVEL - 1;
+constexpr int LAST_PERIOD = GROUP_TERMS / (16 * (LAST_DIAG + 1));
+template <bool PAIR>
+__device__ void mma_last_diagonal(Shared& sh, MmaCtl& c, uint32_t tmem, uint32_t stage0, uint32_t stage_bytes,
+                                  uint32_t boff, int nkb, volatile int* abort) {
+  constexpr uint32_t IDESC = idesc_f16(PAIR ? 2 * TILE_M : TILE_M, BN);
+  constexpr int BPL = PAIR ? BH_BYTES : B_TILE_BYTES;
+  uint32_t buf = acquire(sh, c, abort);
+  uint32_t acc0 = 0u;  // accumulate flag of the first product into the current buffer
+  int left = LAST_PERIOD;
+  for (int kb = 0; kb < nkb; ++kb) {
+    if (left == 0) {
+      post<PAIR>(sh, c, buf);
+      buf = acquire(sh, c, abort);
+      acc0 = 0u;
+      left = LAST_PERIOD;
+    }
+    --left;
+    if (!mbar_wait(bar(&sh.full[c.rg.stg]), (uint32_t)c.rg.ph, abort)) return;
+    const uint32_t aaddr = stage0 + c.rg.stg * stage_bytes;
+    const uint64_t ad0 = smem_desc(aaddr, 128, 128 * KB_CM);
+    const uint64_t bd0 = smem_desc(aaddr + boff, 128, 128 * KB_CM);
+    const uint32_t d = tmem + buf * BN;
+#pragma unroll
+    for (int t = 0; t <= LAST_DIAG; ++t)
+      mma_issue<PAIR, 0>(d, ad0 + (uint64_t)((t * A_TILE_BYTES) >> 4), bd0 + (uint64_t)(((LAST_DIAG - t) * BPL) >> 4),
+                         IDESC, t > 0 ? 1u : acc0);
+    acc0 = 1u;
+    commit_to<PAIR>(bar(&sh.empty[c.rg.stg]));
+    c.rg.advance();
+  }
+  post<PAIR>(sh, c, buf);
+}
+
 // Epilogue side of one drain: wait until the MMAs into buffer b are complete, read this warp's
 // 32 x CW slice, release the buffer, add q * 2^shl into the exact running sums (one 96-bit
 // two's-complement integer w2:w1:w0 per output element).
@@ -241,6 +278,12 @@ __device__ __forceinline__ bool drain_into(Shared& sh, uint32_t tmem, int lq, in
   if (lane == 0) {
     if (remote_release) mbar_arrive_remote(mapa_shared(bar(&sh.acce[b]), 0));
     else mbar_arrive(bar(&sh.acce[b]));
+  }
+  if (shl >= 64) {
+    // level 9, diagonal 0: weight 2^64, the top word alone (the sums are kept modulo 2^96)
+#pragma unroll
+    for (int j = 0; j < CW; ++j) z2[j] += (uint32_t)__float2int_rn(__uint_as_float(v[j]));
+    return true;
   }
 #pragma unroll
   for (int j = 0; j < CW; ++j) w96_add_shifted(z0[j], z1[j], z2[j], __float2int_rn(__uint_as_float(v[j])), shl);
@@ -331,7 +374,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const char* Bb = reinterpret_cast<const char*>(P->B) + (long long)nb * nkb * SB * B_TILE_BYTES +
                          (PAIR ? (long long)rank * SB * BH_BYTES : 0ll);
         bool stop = false;
-        for (int kb = 0; kb < nkb; ++kb) {
+        // one fill per k-block and pass (level 9: the k-blocks twice)
+        const int nfill = passes_of(s) * nkb;
+        for (int f = 0; f < nfill; ++f) {
+          const int kb = f < nkb ? f : f - nkb;
           // a stage is refilled once the MMAs of its previous fill have completed
           if (fills >= nstage && !mbar_wait(bar(&sh.empty[rg.stg]), (uint32_t)(rg.ph ^ 1), abort)) {
             stop = true;
@@ -373,7 +419,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           case 5: mma_tile<5, PAIR>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
           case 6: mma_tile<6, PAIR>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
           case 7: mma_tile<7, PAIR>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
-          case 8: mma_tile<8, PAIR>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort); break;
+          case 8:
+          case 9:  // level 9: the level-8 pass, then diagonal 8 alone
+            mma_tile<8, PAIR>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort);
+            if (P->s == SPLIT_LEVEL) mma_last_diagonal<PAIR>(sh, c, tmem, stage0, stage_bytes, boff, nkb, abort);
+            break;
           default: *abort = 1; break;
         }
       }
@@ -391,7 +441,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         int mb, nb;
         tile_of(tiles, probs, single, idx, P, mb, nb);
         bool stop = false;
-        for (int kb = 0; kb < P->nkb; ++kb) {
+        const int nfill = passes_of(P->s) * P->nkb;
+        for (int f = 0; f < nfill; ++f) {
           if (!mbar_wait(bar(&sh.full[rg.stg]), (uint32_t)rg.ph, abort)) {
             stop = true;
             break;
@@ -428,8 +479,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         else crow = P->C + __ldg(P->rowdst + row) + col0;
       }
       const long long cstr = tmode ? P->ldc : 1;
-      // exact running sum per element, a 96-bit two's-complement integer z2:z1:z0 (|Z| < 2^93 for
-      // levels <= 8 and fewer than 2^13 groups per diagonal)
+      // exact running sum per element, a 96-bit two's-complement integer z2:z1:z0 (|Z| < 2^95 within
+      // the reduction lengths max_k_of_level admits)
       uint32_t z0[CW], z1[CW], z2[CW];
 #pragma unroll
       for (int j = 0; j < CW; ++j) {
@@ -438,31 +489,41 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         z2[j] = 0u;
       }
       bool ok = true;
-      // replay the issuer's schedule: buffers of k-block 0, then mid-tile drains ordered by
-      // (k-block, diagonal), then the final buffers of diagonals 0..S-1
+      // replay the issuer's schedule, pass by pass: the buffers of k-block 0, then the mid-tile
+      // drains ordered by (k-block, diagonal), then the final buffers.  Diagonal g carries the
+      // weight 256^(S-1-g).  Level 9: the first pass takes diagonals 0..7 on the level-8 plan, the
+      // second diagonal 8 alone, drained every LAST_PERIOD k-blocks.
       const int S = P->s, nkb = P->nkb;
       const bool stag = stagger_of(nkb);
-      uint32_t bufs[MAX_LEVEL];
-      int nxt[MAX_LEVEL], per[MAX_LEVEL];
-      for (int g = S - 1; g >= 0; --g) bufs[g] = er.next();
-      for (int g = 0; g < S; ++g) drain_plan(g, S, stag, nxt[g], per[g]);
-      while (ok) {
-        int kbmin = nkb, gsel = -1;
-        for (int g = 0; g < S; ++g)
-          if (nxt[g] < kbmin) {
-            kbmin = nxt[g];
-            gsel = g;
-          }
-        if (gsel < 0) break;
-        ok = drain_into(sh, tmem, lq, cg, lane, bufs[gsel], 8 * (S - 1 - gsel), accf_par, abort, z0, z1, z2,
-                        PAIR && !lead);
-        er.posted(bufs[gsel]);
-        bufs[gsel] = er.next();
-        nxt[gsel] += per[gsel];
-      }
-      for (int g = 0; g < S && ok; ++g) {
-        ok = drain_into(sh, tmem, lq, cg, lane, bufs[g], 8 * (S - 1 - g), accf_par, abort, z0, z1, z2, PAIR && !lead);
-        er.posted(bufs[g]);
+      uint32_t bufs[SPLIT_LEVEL - 1];  // a pass has at most 8 diagonals
+      int nxt[SPLIT_LEVEL - 1], per[SPLIT_LEVEL - 1];
+      for (int pass = 0; pass < passes_of(S) && ok; ++pass) {
+        const int g0 = pass ? SPLIT_LEVEL - 1 : 0;                 // first diagonal of the pass
+        const int nd = pass ? 1 : (S == SPLIT_LEVEL ? S - 1 : S);  // its diagonals
+        for (int d = nd - 1; d >= 0; --d) bufs[d] = er.next();
+        for (int d = 0; d < nd; ++d) {
+          if (pass) nxt[d] = per[d] = LAST_PERIOD;
+          else drain_plan(d, nd, stag, nxt[d], per[d]);
+        }
+        while (ok) {
+          int kbmin = nkb, dsel = -1;
+          for (int d = 0; d < nd; ++d)
+            if (nxt[d] < kbmin) {
+              kbmin = nxt[d];
+              dsel = d;
+            }
+          if (dsel < 0) break;
+          ok = drain_into(sh, tmem, lq, cg, lane, bufs[dsel], 8 * (S - 1 - g0 - dsel), accf_par, abort, z0, z1, z2,
+                          PAIR && !lead);
+          er.posted(bufs[dsel]);
+          bufs[dsel] = er.next();
+          nxt[dsel] += per[dsel];
+        }
+        for (int d = 0; d < nd && ok; ++d) {
+          ok = drain_into(sh, tmem, lq, cg, lane, bufs[d], 8 * (S - 1 - g0 - d), accf_par, abort, z0, z1, z2,
+                          PAIR && !lead);
+          er.posted(bufs[d]);
+        }
       }
       if (!ok) break;
       // ---- one rounding to FP64, scaling; the exact sums pass through shared memory ZC columns at a

@@ -8,7 +8,19 @@ namespace oz {
 constexpr int BN = 64;              // output tile columns (MMA N)
 constexpr int NBUF = 512 / BN;      // TMEM accumulator buffers of BN columns
 
-constexpr int MAX_LEVEL = 8;        // slice levels supported by the BN = 64 kernel (one buffer per diagonal)
+constexpr int MAX_LEVEL = 9;        // slice levels supported by the BN = 64 kernel
+// Levels up to 8 keep one TMEM buffer per diagonal of the slice grid.  Level 9 (nine 64-column
+// accumulators do not fit in TMEM's 512 columns) runs each tile in two passes over its k-blocks:
+// diagonals 0..7, then diagonal 8 alone, both into the same exact sums.
+constexpr int SPLIT_LEVEL = 9;
+__host__ __device__ constexpr int passes_of(int s) { return s == SPLIT_LEVEL ? 2 : 1; }
+// Longest reduction of one product.  The exact sum of an output element is bounded by
+// K 2^14 sum_g (g+1) 2^(8(s-1-g)) (digit products are at most 2^14 in magnitude) and must stay below
+// 2^95, the range of the epilogue's 96-bit sums: any K <= 2^20 at levels up to 8, K <= 130,048
+// (= 8128 k-blocks of 16) at level 9.
+constexpr long long MAX_K = 1ll << 20;
+constexpr long long MAX_K_LEVEL9 = 130048;
+inline long long max_k_of_level(int s) { return s >= SPLIT_LEVEL ? MAX_K_LEVEL9 : MAX_K; }
 
 // output modes: dense C[row * ldc + col]; row table (C + rowdst[row] + col, with per-row |max|);
 // dense transposed C[col * ldc + row]

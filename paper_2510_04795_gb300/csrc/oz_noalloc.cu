@@ -64,11 +64,13 @@ extern "C" int ozaki_gemm_noalloc(int m, int n, int k, double alpha, const doubl
                                   oz_stream_t stream) {
   if (slices < 1 || slices > 9) return fail(OZ_EINVAL, "slices must be in 1..9");
   const int s = level == 0 ? slices : level;
-  if (s < 1 || s > slices || s > oz::MAX_LEVEL) return fail(OZ_EINVAL, "level must be in 1..min(S,8)");
+  if (s < 1 || s > slices || s > oz::MAX_LEVEL) return fail(OZ_EINVAL, "level must be in 1..S");
   if (m < 0 || n < 0 || k < 0) return fail(OZ_EINVAL, "negative size");
   if (lda < (k > 1 ? k : 1) || ldb < (n > 1 ? n : 1) || ldc < (n > 1 ? n : 1))
     return fail(OZ_EINVAL, "leading dimension too small");
-  if (k > (1 << 20)) return fail(OZ_EINVAL, "k exceeds the exact-accumulation limit (1048576)");
+  if (k > oz::max_k_of_level(s))
+    return fail(OZ_EINVAL, s >= oz::SPLIT_LEVEL ? "k exceeds the exact-accumulation limit of level 9 (130048)"
+                                                : "k exceeds the exact-accumulation limit (1048576)");
   if (m == 0 || n == 0) return OZ_OK;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return fail(OZ_ECUDA, "cudaGetDevice failed");

@@ -30,6 +30,8 @@ namespace {
 constexpr int NBIN = 9;  // gap bins 0, 1, 2-3, 4-7, 8-15, 16-31, 32-63, >= 64, and exact zeros
 constexpr int NF = OZ_NFEAT;
 constexpr int LMIN = 3;  // lowest level a selector picks
+constexpr int LPRED = 8; // highest level with a predicted error; a handle at level 9 (the fixed
+                         // fallback) starts there with its error counted as zero
 
 struct HistSeg {
   const double* p;
@@ -341,7 +343,7 @@ extern "C" int oz_heff_select_levels(oz_heff* h, const double* d_psi, int select
   if (h->mode != OZ_MODE_EAGER) return oz::api_fail(OZ_EINVAL, "levels exist for emulated handles only");
   if (selector < OZ_SELECT_FIXED || selector > OZ_SELECT_LEARNED) return oz::api_fail(OZ_EINVAL, "unknown selector");
   if (!(budget > 0.0)) return oz::api_fail(OZ_EINVAL, "budget must be positive");
-  if (selector == OZ_SELECT_LEARNED && (!net || oz_mlp_nin(net) != NF || oz_mlp_nout(net) < oz::MAX_LEVEL - LMIN + 1))
+  if (selector == OZ_SELECT_LEARNED && (!net || oz_mlp_nin(net) != NF || oz_mlp_nout(net) < LPRED - LMIN + 1))
     return oz::api_fail(OZ_EINVAL, "the learned selector needs a network with OZ_NFEAT inputs and 6 outputs");
   cudaStream_t st = (cudaStream_t)stream;
   const int nsec = h->nsec, smax = h->s;
@@ -369,8 +371,8 @@ extern "C" int oz_heff_select_levels(oz_heff* h, const double* d_psi, int select
         t2 += nr[2 * i + 1];
       }
     }
-    // predicted log10 errors for levels LMIN..MAX_LEVEL
-    const int nl = oz::MAX_LEVEL - LMIN + 1;
+    // predicted log10 errors for levels LMIN..LPRED
+    const int nl = LPRED - LMIN + 1;
     std::vector<float> pred((size_t)2 * nsec * nl, 0.0f);
     if (selector == OZ_SELECT_ANALYTIC) {
       for (int stage = 0; stage < 2; ++stage)
@@ -414,7 +416,7 @@ extern "C" int oz_heff_select_levels(oz_heff* h, const double* d_psi, int select
         size[q] = 2.0 * std::ceil(M / oz::TILE_M) * oz::TILE_M * std::ceil(Nn / oz::BN) * oz::BN * K;
       }
       auto err2 = [&](int q, int l) {
-        if (on[q] <= 0.0) return 0.0;
+        if (on[q] <= 0.0 || l > LPRED) return 0.0;
         const double e = std::pow(10.0, pred[((size_t)stage * nsec + q) * nl + (l - LMIN)] + margin);
         return e * e * on[q];
       };

@@ -32,20 +32,14 @@ __device__ __forceinline__ const SliceSeg& find_seg(const SliceSeg* segs, const 
   return base[lo];
 }
 
-__device__ __forceinline__ double load_src(const SliceSeg& g, int i, int j) {
-  long long off = g.trans ? (long long)j * g.ld + i : (long long)i * g.ld + j;
-  double v = __ldg(g.src + off);
-  return g.scale != 1.0 ? __dmul_rn(v, g.scale) : v;
-}
-
 __device__ __forceinline__ unsigned long long absbits(double v) {
   return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
 }
 
 // Row maxima, two access patterns chosen per segment so that every warp load is coalesced:
-//  * trans == 0 (rows contiguous in memory): one warp per (RM_ROWS rows, RM_CHUNK columns); for
-//    each of its rows lane l reads columns l, l + 32, ... (256 consecutive bytes per warp load,
-//    four loads in flight per lane), then a warp-shuffle max and one atomicMax per row;
+//  * trans == 0 (rows contiguous in memory): one warp per (RM_ROWS rows, RM_CHUNK columns); lane l
+//    reads columns l, l + 32, ... of all its rows together (256 consecutive bytes per warp load,
+//    2 RM_ROWS loads in flight per lane), then a warp-shuffle max and one atomicMax per row;
 //  * trans == 1 (consecutive rows adjacent in memory): one thread per (row, ROWMAX_SPAN
 //    columns), consecutive threads on consecutive rows (256 consecutive bytes per warp load).
 // Segment slot counts are multiples of 32, so no warp straddles two segments.
@@ -57,13 +51,16 @@ __device__ __forceinline__ unsigned long long scaled_max(unsigned long long mb, 
   return absbits(__dmul_rn(__longlong_as_double((long long)mb), fabs(c)));
 }
 
-__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
-    v = w > v ? w : v;
-  }
-  return v;
+// |x| as 32-bit halves (x = lo, y = hi) of its bit pattern
+__device__ __forceinline__ uint2 ldg_bits(const double* p) {
+  const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+  return make_uint2(v.x, v.y & 0x7FFFFFFFu);
+}
+// (mh, ml) = max((mh, ml), v) in the order of the 64-bit patterns, with 32-bit comparisons
+__device__ __forceinline__ void max_hl(uint32_t& mh, uint32_t& ml, uint2 v) {
+  const bool gt = v.y > mh || (v.y == mh && v.x > ml);
+  mh = gt ? v.y : mh;
+  ml = gt ? v.x : ml;
 }
 
 __global__ void __launch_bounds__(256) rowmax_kernel(const SliceSeg* __restrict__ segs,
@@ -80,28 +77,65 @@ __global__ void __launch_bounds__(256) rowmax_kernel(const SliceSeg* __restrict_
     const int lane = (int)(lu & 31);
     const long long w = lu >> 5;
     const int nch = (g.cols + RM_CHUNK - 1) / RM_CHUNK;
-    const int r0 = (int)(w / nch) * RM_ROWS, r1 = min(g.rows, r0 + RM_ROWS);
+    const int r0 = (int)(w / nch) * RM_ROWS, nr = min(g.rows - r0, RM_ROWS);
     const int j0 = (int)(w % nch) * RM_CHUNK, j1 = min(g.cols, j0 + RM_CHUNK);
-    for (int r = r0; r < r1; ++r) {
-      const double* rp = g.src + (long long)r * g.ld;
-      unsigned long long m = 0;
-      int j = j0 + lane;
-      for (; j + 96 < j1; j += 128) {
-        const unsigned long long b0 = absbits(__ldg(rp + j)), b1 = absbits(__ldg(rp + j + 32));
-        const unsigned long long b2 = absbits(__ldg(rp + j + 64)), b3 = absbits(__ldg(rp + j + 96));
-        const unsigned long long m01 = b0 > b1 ? b0 : b1, m23 = b2 > b3 ? b2 : b3;
-        const unsigned long long mm = m01 > m23 ? m01 : m23;
-        m = mm > m ? mm : m;
+    const double* rp = g.src + (long long)r0 * g.ld;
+    // all rows of the warp at once: 2 RM_ROWS loads in flight per lane whatever the row length.
+    // (16-byte loads of aligned column pairs were measured slower: their registers halve the
+    // resident warps.)  The maxima are kept as 32-bit halves and compared with 32-bit integer
+    // operations only: the magnitudes are non-negative, so (hi, lo) order is the 64-bit order.
+    uint32_t mh[RM_ROWS], ml[RM_ROWS];
+#pragma unroll
+    for (int r = 0; r < RM_ROWS; ++r) mh[r] = ml[r] = 0u;
+    int j = j0 + lane;
+    for (; j + 32 < j1; j += 64) {
+      uint2 b0[RM_ROWS], b1[RM_ROWS];
+#pragma unroll
+      for (int r = 0; r < RM_ROWS; ++r) {
+        b0[r] = r < nr ? ldg_bits(rp + r * g.ld + j) : make_uint2(0u, 0u);
+        b1[r] = r < nr ? ldg_bits(rp + r * g.ld + j + 32) : make_uint2(0u, 0u);
       }
-      for (; j < j1; j += 32) {
-        const unsigned long long b = absbits(__ldg(rp + j));
-        m = b > m ? b : m;
+#pragma unroll
+      for (int r = 0; r < RM_ROWS; ++r) {
+        max_hl(mh[r], ml[r], b0[r]);
+        max_hl(mh[r], ml[r], b1[r]);
       }
-      m = scaled_max(warp_max_u64(m), g.scale);
-      if (lane == 0) {
-        if (m >= 0x7FF0000000000000ull) atomicOr(flags, 1);  // Inf or NaN in the input
-        if (m) atomicMax(g.rowmax + g.r0 + r, m);
+    }
+    if (j < j1) {
+#pragma unroll
+      for (int r = 0; r < RM_ROWS; ++r)
+        if (r < nr) max_hl(mh[r], ml[r], ldg_bits(rp + r * g.ld + j));
+    }
+    // 8 row maxima over 32 lanes in 3 halving exchanges and 2 plain ones: after the exchange over
+    // lane bit 16 (8, 4) a lane keeps the half of its rows selected by that bit, so lane 4k ends
+    // with the maximum of row k over all lanes
+    static_assert(RM_ROWS == 8, "the exchange below reduces 8 rows");
+#pragma unroll
+    for (int o = 16, n = RM_ROWS; o >= 4; o >>= 1, n >>= 1) {
+      const bool hi = (lane & o) != 0;
+#pragma unroll
+      for (int i = 0; i < RM_ROWS / 2; ++i) {
+        if (i < n / 2) {
+          const uint32_t sh = hi ? mh[i] : mh[i + n / 2], sl = hi ? ml[i] : ml[i + n / 2];
+          const uint32_t kh = hi ? mh[i + n / 2] : mh[i], kl = hi ? ml[i + n / 2] : ml[i];
+          const uint2 recv = make_uint2(__shfl_xor_sync(0xffffffffu, sl, o), __shfl_xor_sync(0xffffffffu, sh, o));
+          mh[i] = kh;
+          ml[i] = kl;
+          max_hl(mh[i], ml[i], recv);
+        }
       }
+    }
+#pragma unroll
+    for (int o = 2; o > 0; o >>= 1) {
+      const uint2 recv = make_uint2(__shfl_xor_sync(0xffffffffu, ml[0], o), __shfl_xor_sync(0xffffffffu, mh[0], o));
+      max_hl(mh[0], ml[0], recv);
+    }
+    const unsigned long long m0 = ((unsigned long long)mh[0] << 32) | ml[0];
+    const int r = lane >> 2;
+    if ((lane & 3) == 0 && r < nr) {
+      const unsigned long long mm = scaled_max(m0, g.scale);
+      if (mm >= 0x7FF0000000000000ull) atomicOr(flags, 1);  // Inf or NaN in the input
+      if (mm) atomicMax(g.rowmax + g.r0 + r0 + r, mm);
     }
     return;
   } else {
@@ -110,11 +144,9 @@ __global__ void __launch_bounds__(256) rowmax_kernel(const SliceSeg* __restrict_
     row = (int)(lu % g.rows);
     const int sp = (int)(lu / g.rows);
     const int j0 = sp * ROWMAX_SPAN, j1 = min(g.cols, j0 + ROWMAX_SPAN);
-    for (int j = j0; j < j1; ++j) {
-      const unsigned long long b = absbits(__ldg(g.src + (long long)j * g.ld + row));
-      mx = b > mx ? b : mx;
-    }
-    mx = scaled_max(mx, g.scale);
+    uint32_t mh = 0u, ml = 0u;
+    for (int j = j0; j < j1; ++j) max_hl(mh, ml, ldg_bits(g.src + (long long)j * g.ld + row));
+    mx = scaled_max(((unsigned long long)mh << 32) | ml, g.scale);
   }
   if (row < 0) return;
   if (mx >= 0x7FF0000000000000ull) atomicOr(flags, 1);  // Inf or NaN in the input
@@ -155,36 +187,51 @@ __global__ void __launch_bounds__(256) digits_kernel(const SliceSeg* __restrict_
   if (u >= total) return;
   int r8 = (int)(tid & 7);
   const SliceSeg& g = find_seg<false>(segs, pack, nseg, u, ctaseg);
-  long long lu = u - g.unit0;
-  int nkc = (g.pcols + 7) >> 3;
-  int rg = (int)(lu / nkc), c = (int)(lu % nkc);
+  // unit -> (8-row group, 8-column chunk) of the segment, by 32-bit division: a segment's source is
+  // resident FP64 data (below 2^35 elements in 288 GB), so it has fewer than 2^30 units of 64 elements
+  const uint32_t lu = (uint32_t)(u - g.unit0);
+  const uint32_t nkc = (uint32_t)(g.pcols + 7) >> 3;
+  const uint32_t rgi = lu / nkc;
+  const int rg = (int)rgi, c = (int)(lu - rgi * nkc);
   int i = rg * 8 + r8;
   if (i >= g.prows) return;
   int R = g.r0 + i;
   const bool rowok = i < g.rows;
+  const bool scaled = g.scale != 1.0;  // one FP64 compare per thread
   int e = rowok ? exponent_from_maxbits(g.rowmax[R]) : 0;
   if (c == 0) g.rowexp[R] = e;
   // the 8 values: one 64-byte run of the row, read as four 16-byte loads where it is aligned
   double vals[8];
   const int j0 = c * 8;
-  const double* rp = g.src + (long long)i * g.ld + j0;
-  if (rowok && !g.trans && j0 + 8 <= g.cols && ((reinterpret_cast<uintptr_t>(rp) & 15) == 0)) {
+  if (!rowok) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const double2 w = __ldg(reinterpret_cast<const double2*>(rp) + q);
-      vals[2 * q] = w.x;
-      vals[2 * q + 1] = w.y;
-    }
-    if (g.scale != 1.0) {
+    for (int q = 0; q < 8; ++q) vals[q] = 0.0;
+  } else if (!g.trans) {
+    const double* rp = g.src + (long long)i * g.ld + j0;
+    if (j0 + 8 <= g.cols && ((reinterpret_cast<uintptr_t>(rp) & 15) == 0)) {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) vals[q] = __dmul_rn(vals[q], g.scale);
+      for (int q = 0; q < 4; ++q) {
+        const double2 w = __ldg(reinterpret_cast<const double2*>(rp) + q);
+        vals[2 * q] = w.x;
+        vals[2 * q + 1] = w.y;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) vals[q] = j0 + q < g.cols ? __ldg(rp + q) : 0.0;
     }
   } else {
+    const double* cp = g.src + (long long)j0 * g.ld + i;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) vals[q] = (rowok && j0 + q < g.cols) ? load_src(g, i, j0 + q) : 0.0;
+    for (int q = 0; q < 8; ++q) vals[q] = j0 + q < g.cols ? __ldg(cp + (long long)q * g.ld) : 0.0;
+  }
+  if (scaled) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) vals[q] = __dmul_rn(vals[q], g.scale);
   }
   int K = g.k0 + c * 8;
-  int rt = R / g.TR, rr = R % g.TR, kb = K >> KB_SHIFT, kk = K & (KB - 1);
+  // TR is 64 or 128
+  const int trs = g.TR == 128 ? 7 : 6;
+  int rt = R >> trs, rr = R & (g.TR - 1), kb = K >> KB_SHIFT, kk = K & (KB - 1);
   // plane t of (row, k) at base + t * pstride; a half-major operand stores the 32-row halves of each
   // k-block of a tile one after the other (each half: S planes of 32 rows)
   long long base;

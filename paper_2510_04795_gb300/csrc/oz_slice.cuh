@@ -22,7 +22,7 @@ struct SliceSeg {
   int S;                       // digit planes stored by the operand
   double scale;
   __half* dst;                 // tiled planes: [row tile][k-block][plane][TR x 32 halves]
-  int TR;                      // rows per tile of the operand (128 for A, BN for B)
+  int TR;                      // rows per tile of the operand: 128 for A, BN = 64 for B
   int nkb;                     // k-blocks of the operand
   unsigned long long* rowmax;  // per operand row: bit pattern of max |value|
   int* rowexp;                 // per operand row: shared exponent (written by the digit pass)

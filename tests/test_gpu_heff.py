@@ -30,7 +30,8 @@ def _tasks(st, blocks):
 
 @pytest.mark.parametrize("tile", ["cta", "pair"])
 @pytest.mark.parametrize("seed,grid,dims,S,s", [(1, (3, 3), (2, 20), 7, 7), (2, (4, 3), (5, 70), 4, 4),
-                                               (3, (3, 2), (60, 140), 9, 6), (4, (4, 4), (30, 300), 7, 7)])
+                                               (3, (3, 2), (60, 140), 9, 6), (4, (4, 4), (30, 300), 7, 7),
+                                               (3, (3, 2), (60, 140), 9, 9)])
 def test_heff_bitexact_vs_emulated_oracle(ctx, seed, grid, dims, S, s, tile):
     """Both tilings of the products (128 x 64 on one CTA; 256 x 64 on a CTA pair, with the pair's
     padding tile of odd operands and both stage-2 orientations) give the oracle's bits."""

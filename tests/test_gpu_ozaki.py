@@ -75,6 +75,10 @@ CASES = [
     (33, 2050, 17, 2, 2),
     (40, 40, 40, 1, 1),
     (256, 64, 192, 4, 6),
+    (7, 9, 5, 9, 9),          # level 9: two passes per tile (diagonals 0..7, then diagonal 8)
+    (129, 33, 65, 9, 9),
+    (64, 1100, 70, 9, 9),     # level 9, long K: staggered drains in the first pass, drains of
+                              # diagonal 8 every 7 k-blocks in the second
 ]
 
 
@@ -129,7 +133,28 @@ def test_gemm_rejects_bad_arguments(ctx):
         oz.ozaki_gemm(ctx, A, A, slices=10)
     assert ei.value.code == 1
     with pytest.raises(oz.OzError):
-        oz.ozaki_gemm(ctx, A, A, slices=9, level=9)   # level 9 needs 9 accumulators
+        oz.ozaki_gemm(ctx, A, A, slices=8, level=9)   # level above the stored depth
+
+
+def test_gemm_level9_largest_sum_at_the_k_limit(ctx):
+    """Level 9 at its longest reduction, K = 130,048, on the largest exact sum the 96-bit epilogue
+    sums can meet: every value 127/128 (its own row maximum, leading digit 127), so each output is
+    K * (127/128)^2 exactly, |Z| = K 127^2 2^64 just below 2^95.  One more column is refused at
+    level 9 and accepted at level 8."""
+    import paper_2510_04795_gb300 as oz
+    k = 130048
+    A = torch.full((3, k), 127.0 / 128.0, dtype=torch.float64, device="cuda")
+    B = torch.full((k, 2), -127.0 / 128.0, dtype=torch.float64, device="cuda")
+    C = oz.ozaki_gemm(ctx, A, B, slices=9, level=9)
+    ctx.status()
+    assert torch.all(C == -k * (127.0 / 128.0) ** 2)
+    A1 = torch.full((3, k + 1), 127.0 / 128.0, dtype=torch.float64, device="cuda")
+    B1 = torch.full((k + 1, 2), -127.0 / 128.0, dtype=torch.float64, device="cuda")
+    with pytest.raises(oz.OzError):
+        oz.ozaki_gemm(ctx, A1, B1, slices=9, level=9)
+    C8 = oz.ozaki_gemm(ctx, A1, B1, slices=9, level=8)
+    ctx.status()
+    assert torch.all(C8 == -(k + 1) * (127.0 / 128.0) ** 2)
 
 
 def test_nonfinite_input_reported(ctx):
