@@ -29,8 +29,8 @@ FALLBACK_PEAK = {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gb
 
 # DRAM bytes per algorithmic carrier flop of the GEMM kernel, from one ncu capture, and the
 # digest of the kernel source it was taken on (the figure is dropped once the source changes).
-NCU_TRAFFIC = {"bytes_per_carrier_flop": 0.0021531,
-               "gemm_source_sha256": "fcfed12a27c9d88e4f92d33603fb36ba68a6a0b51eef92d954b03f58baf1962c"}
+NCU_TRAFFIC = {"bytes_per_carrier_flop": 0.0021547,
+               "gemm_source_sha256": "905b3f1562502299b9641cd404256f295c5bdd461b7d1918e407c99db6b13a33"}
 
 
 def parse():

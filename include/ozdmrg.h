@@ -254,6 +254,18 @@ int oz_heff_autotune(oz_heff* h, const double* d_psi, int reps, int* sched, floa
 int oz_heff_partition(int nsec, const int* m, const int* n, int ntask, const int* src, const int* dst, int world,
                       int* owner);
 int oz_reduce_ordered(const double* const* d_parts, int nparts, long long len, double* d_out, oz_stream_t stream);
+/* The term-sharded product on ONE GPU, for structures whose operator digit planes do not fit in
+ * device memory at once (oz_heff_create fails with OZ_ENOMEM): the tasks are split into `chunks`
+ * groups by oz_heff_partition (world = chunks); for each group in turn a handle is built (its
+ * operators sliced), its partial product computed and the handle destroyed; the partial vectors
+ * are summed in group order as in oz_reduce_ordered.  d_y (dim doubles, dim = sum_q m[q] n[q])
+ * then holds exactly what the sharded product over `chunks` ranks reduces to.  Every call slices
+ * every operator again; peak device memory is one group's handle plus one partial vector.  prec
+ * as for oz_heff_create; chunks = 1 is one handle's product.  Synchronises the stream.  Errors:
+ * those of oz_heff_create and heff_apply (OZ_ENOMEM when even one group does not fit),
+ * OZ_EINVAL for chunks < 1. */
+int oz_heff_apply_streamed(oz_ctx* ctx, int nsec, const int* m, const int* n, int ntask, const oz_task* tasks,
+                           const oz_prec* prec, int chunks, const double* d_psi, double* d_y, oz_stream_t stream);
 
 /* ------------------------------------------------------------------------------------------
  * Slice-level selection per block (the precision dial of sections "Theory of emulated FP64

@@ -321,6 +321,26 @@ def reduce_ordered(parts, out: torch.Tensor | None = None, stream=None) -> torch
     return out
 
 
+def heff_apply_streamed(ctx: Context, m, n, tasks, psi: torch.Tensor, chunks: int, y: torch.Tensor | None = None,
+                        slices=7, level=0, mode="eager", stream=None) -> torch.Tensor:
+    """H_eff psi for structures whose operator digits do not fit on the device at once
+    (``oz_heff_apply_streamed``): the tasks split into ``chunks`` groups as ``heff_partition`` splits
+    them over ranks, each group's handle built, applied and released in turn, the partial products
+    summed in group order -- the term-sharded product over ``chunks`` ranks, on one GPU."""
+    _check_f64(psi)
+    m = [int(x) for x in m]
+    n = [int(x) for x in n]
+    if y is None:
+        y = torch.empty_like(psi)
+    _check_f64(y)
+    nsec = len(m)
+    p = _prec(slices, level, mode)
+    N.check(ctx.lib.oz_heff_apply_streamed(ctx.h, nsec, (C.c_int * nsec)(*m), (C.c_int * nsec)(*n), len(tasks),
+                                           _task_array(tasks), C.byref(p), int(chunks), _ptr(psi), _ptr(y),
+                                           _stream(stream)))
+    return y
+
+
 class ShardedHeff:
     """This rank's share of a term-sharded H_eff: a handle built from the tasks that
     ``heff_partition`` gives to ``rank``; ``apply`` computes the partial product, gathers the

@@ -124,6 +124,8 @@ def load():
         "oz_heff_partition": (i, [i, vp, vp, i, vp, vp, i, vp]),
         "oz_heff_ops_times": (i, [vp, vp, vp]),
         "oz_reduce_ordered": (i, [vp, i, ll, vp, vp]),
+        "oz_heff_apply_streamed": (i, [vp, i, C.POINTER(i), C.POINTER(i), i, C.POINTER(oz_task), C.POINTER(oz_prec),
+                                       i, vp, vp, vp]),
         "oz_dmrg_trace": (i, [vp, ll, vp, vp, vp, vp, C.POINTER(ll)]),
         "dmrg_sweep": (i, [vp, vp, vp, i, i, i, i, i, C.POINTER(oz_prec), d, C.c_ulonglong, vp]),
     }

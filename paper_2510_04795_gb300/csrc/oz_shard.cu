@@ -11,6 +11,9 @@
 //    the least work so far (ties to the lower rank, equal costs in task order).
 //  * oz_reduce_ordered: out = ((p_0 + p_1) + p_2) + ... in FP64, element by element in rank
 //    order, so the reduced vector does not depend on the order in which the parts arrived.
+//  * oz_heff_apply_streamed: the same split on ONE GPU for structures whose operator digit planes
+//    do not fit at once: the groups of the partition are built, applied and released one after
+//    the other, their partial vectors summed in group order as they come.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -87,4 +90,58 @@ extern "C" int oz_reduce_ordered(const double* const* d_parts, int nparts, long 
   e = cudaGetLastError();
   if (e != cudaSuccess) return oz::api_fail(OZ_ECUDA, std::string("reduce_ordered: ") + cudaGetErrorString(e));
   return OZ_OK;
+}
+
+extern "C" int oz_heff_apply_streamed(oz_ctx* ctx, int nsec, const int* m, const int* n, int ntask,
+                                      const oz_task* tasks, const oz_prec* prec, int chunks, const double* d_psi,
+                                      double* d_y, oz_stream_t stream) {
+  if (!ctx || !prec || !d_psi || !d_y) return oz::api_fail(OZ_EINVAL, "null argument");
+  if (chunks < 1) return oz::api_fail(OZ_EINVAL, "chunks must be >= 1");
+  if (nsec <= 0 || ntask < 0 || !m || !n || (ntask > 0 && !tasks)) return oz::api_fail(OZ_EINVAL, "bad structure");
+  long long dim = 0;
+  for (int q = 0; q < nsec; ++q) {
+    if (m[q] <= 0 || n[q] <= 0) return oz::api_fail(OZ_EINVAL, "sector dims must be positive");
+    dim += (long long)m[q] * n[q];
+  }
+  std::vector<int> src(ntask), dst(ntask), owner(ntask);
+  for (int t = 0; t < ntask; ++t) {
+    src[t] = tasks[t].src;
+    dst[t] = tasks[t].dst;
+  }
+  if (int rc = oz_heff_partition(nsec, m, n, ntask, src.data(), dst.data(), chunks, owner.data())) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* part = nullptr;  // the partial product of one group
+  if (chunks > 1) {
+    cudaError_t e = cudaMalloc(&part, (size_t)std::max(dim, 1ll) * 8);
+    if (e != cudaSuccess)
+      return oz::api_fail(e == cudaErrorMemoryAllocation ? OZ_ENOMEM : OZ_ECUDA, "streamed partial vector");
+  }
+  int rc = OZ_OK;
+  std::vector<oz_task> group;
+  group.reserve(ntask);
+  for (int r = 0; r < chunks && rc == OZ_OK; ++r) {
+    group.clear();
+    for (int t = 0; t < ntask; ++t)
+      if (owner[t] == r) group.push_back(tasks[t]);
+    // group 0 writes d_y; every later group writes its partial and is added in group order
+    double* out = r == 0 ? d_y : part;
+    oz_heff* h = nullptr;
+    rc = oz_heff_create(ctx, nsec, m, n, (int)group.size(), group.data(), prec, &h);
+    if (rc == OZ_OK) rc = heff_apply(h, d_psi, out, stream);
+    if (rc == OZ_OK) rc = oz_status(ctx, stream);  // surfaces device-side conditions of the group
+    if (h) {
+      const int rd = oz_heff_destroy(h);
+      if (rc == OZ_OK) rc = rd;
+    }
+    if (rc == OZ_OK && r > 0) {
+      const double* pp[2] = {d_y, part};
+      rc = oz_reduce_ordered(pp, 2, dim, d_y, stream);
+    }
+  }
+  if (part) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFree(part);
+    if (rc == OZ_OK && e != cudaSuccess) rc = oz::api_fail(OZ_ECUDA, std::string("streamed: ") + cudaGetErrorString(e));
+  }
+  return rc;
 }

@@ -62,3 +62,37 @@ def test_reduce_ordered_edge_cases():
     assert torch.equal(out, (x + x) + x)
     with pytest.raises(OzError):
         oz.reduce_ordered([x] * 65)
+
+
+@pytest.mark.parametrize("chunks", [1, 3])
+def test_streamed_product_is_the_sharded_sum(chunks):
+    """oz_heff_apply_streamed on one GPU: the groups of the partition built, applied and released in
+    turn give, bit for bit, the oracle's emulated product of every group summed in group order (for
+    one chunk: the single handle's product)."""
+    import paper_2510_04795_gb300 as oz
+    ctx = oz.Context(0)
+    st = synthetic.heff_structure(grid=(4, 4), dims=(8, 96), nterms=16, spread=True, seed=9)
+    blocks = [tuple(b.cuda() for b in synthetic.gen_task_blocks(st, t)) for t in range(st.ntask)]
+    psi = synthetic.gen_psi(st).cuda()
+    tasks = [(int(s), int(d), float(st.term_coef[k]), L, R) for (k, s, d), (L, R) in zip(st.tasks, blocks)]
+    Lb = [b[0].cpu().numpy() for b in blocks]
+    Rb = [b[1].cpu().numpy() for b in blocks]
+    psi_h = psi.cpu().numpy()
+    y = oz.heff_apply_streamed(ctx, st.m, st.n, tasks, psi, chunks, slices=7)
+    ctx.status()
+    owner = oz.heff_partition(st.m, st.n, [t[0] for t in tasks], [t[1] for t in tasks], chunks)
+    acc = None
+    for r in range(chunks):
+        ids = np.flatnonzero(owner == r)
+        sub = synthetic.HeffStructure(st.labels, st.m, st.n, st.term_delta, st.term_coef, st.tasks[ids], st.spread,
+                                      st.seed)
+        ref = heff.heff_apply_emulated(sub, [Lb[i] for i in ids], [Rb[i] for i in ids], psi_h, 7)
+        acc = ref if acc is None else acc + ref
+    assert np.array_equal(y.cpu().numpy().view(np.int64), acc.view(np.int64))
+    if chunks == 1:
+        h = oz.Heff(ctx, st.m, st.n, tasks, slices=7)
+        assert torch.equal(h.apply(psi), y)
+        h.close()
+    with pytest.raises(oz.OzError):
+        oz.heff_apply_streamed(ctx, st.m, st.n, tasks, psi, 0)
+    ctx.close()
