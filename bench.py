@@ -29,8 +29,8 @@ FALLBACK_PEAK = {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gb
 
 # DRAM bytes per algorithmic carrier flop of the GEMM kernel, from one ncu capture, and the
 # digest of the kernel source it was taken on (the figure is dropped once the source changes).
-NCU_TRAFFIC = {"bytes_per_carrier_flop": 0.0021547,
-               "gemm_source_sha256": "905b3f1562502299b9641cd404256f295c5bdd461b7d1918e407c99db6b13a33"}
+NCU_TRAFFIC = {"bytes_per_carrier_flop": 0.0021576,
+               "gemm_source_sha256": "0e0a4d645c357bc194948dbb1034c28963c7539a38d11ef7911d8ada3bb4d668"}
 
 
 def parse():

@@ -233,18 +233,6 @@ OZ_DEVICE_INLINE int exponent_from_maxbits(unsigned long long mb) {
   return (f > (63ull << 46)) ? ex + 1 : ex;  // m <= 127/128  <=>  f <= 63 * 2^46
 }
 
-// RN_even(|x| * 2^sh) for the 53-bit significand M of x and a shift sh; exact integer result.
-OZ_DEVICE_INLINE unsigned long long round_shift(unsigned long long M, int sh) {
-  if (sh >= 0) return M << sh;               // caller guarantees no overflow
-  int r = -sh;
-  if (r >= 64) return 0ull;
-  unsigned long long q = M >> r;
-  unsigned long long rem = M & ((1ull << r) - 1);
-  unsigned long long half = 1ull << (r - 1);
-  if (rem > half || (rem == half && (q & 1ull))) ++q;
-  return q;
-}
-
 // RN_even(Z * 2^E) as IEEE binary64, Z a signed 128-bit integer.
 static __device__ __noinline__ double int128_to_double(__int128 Z, int E) {
   if (Z == 0) return 0.0;

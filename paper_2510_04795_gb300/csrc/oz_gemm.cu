@@ -532,7 +532,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int ea = ea_raw - 8 * S - 6;
       const double alpha = P->alpha, beta = P->beta;
       const bool plain = (mode == OUT_ROWTABLE) || ((alpha == 1.0) && (beta == 0.0));
-      unsigned long long mx = 0;
+      // row-table mode: max |value| of the row's outputs, as 32-bit halves of the bit pattern
+      // (compared with 32-bit integer operations; 64-bit comparisons would issue to the FP64 pipe)
+      const bool tabmax = mode == OUT_ROWTABLE && P->rowmax;
+      uint32_t mxh = 0u, mxl = 0u;
 #pragma unroll
       for (int c4 = 0; c4 < CW / ZC; ++c4) {
         if (c4 * ZC < ncol) {
@@ -553,8 +556,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 v = __dmul_rn(alpha, v);
                 if (beta != 0.0) v = __dadd_rn(v, __dmul_rn(beta, crow[jj * cstr]));
               }
-              const unsigned long long bb = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
-              mx = bb > mx ? bb : mx;
+              if (tabmax) {
+                const uint32_t bh = (uint32_t)__double2hiint(v) & 0x7FFFFFFFu, bl = (uint32_t)__double2loint(v);
+                const bool gt = bh > mxh || (bh == mxh && bl > mxl);
+                mxh = gt ? bh : mxh;
+                mxl = gt ? bl : mxl;
+              }
               // transposed output: the warp's lanes are consecutive rows, i.e. consecutive addresses
               if (tmode) crow[jj * cstr] = v;
             }
@@ -572,7 +579,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           __syncwarp();
         }
       }
-      if (mode == OUT_ROWTABLE && rowok && mx && P->rowmax) atomicMax(P->rowmax + __ldg(P->rowslot + row), mx);
+      if (tabmax && rowok && (mxh | mxl))
+        atomicMax(P->rowmax + __ldg(P->rowslot + row), ((unsigned long long)mxh << 32) | mxl);
     }
   }
 

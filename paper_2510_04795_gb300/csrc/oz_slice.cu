@@ -153,12 +153,25 @@ __global__ void __launch_bounds__(256) rowmax_kernel(const SliceSeg* __restrict_
   if (mx) atomicMax(g.rowmax + g.r0 + row, mx);
 }
 
+// RN_even(|x| * 2^sh) for the 53-bit significand M of x and a shift sh; exact integer result.
+// A right shift by r rounds to nearest even as floor((M + 2^(r-1) - 1 + q0) / 2^r), q0 the lowest
+// bit of the truncated quotient: a remainder below the half stays below 2^r, above it reaches
+// 2^r, and exactly the half rounds up only when q0 = 1.  (No 64-bit comparisons: on this GPU those
+// issue to the FP64 pipe.)  M < 2^53, so M + 2^62 does not overflow.
+__device__ __forceinline__ unsigned long long round_shift(unsigned long long M, int sh) {
+  if (sh >= 0) return M << sh;  // caller guarantees no overflow
+  const int r = -sh;
+  if (r >= 64) return 0ull;     // M < 2^53 <= 2^(r-1): below the half
+  const unsigned long long q0 = (M >> r) & 1ull;
+  return (M + ((1ull << (r - 1)) - 1ull) + q0) >> r;
+}
+
 // fixed point of one value: X = RN_even(|x| 2^(8S-1-e)) with sign; S <= 8 (fits int64)
 __device__ __forceinline__ long long fixed_point64(double x, int e, int S) {
   unsigned long long b = (unsigned long long)__double_as_longlong(x);
   int be = (int)((b >> 52) & 0x7FF);
   unsigned long long f = b & ((1ull << 52) - 1);
-  if (be == 0 && f == 0) return 0;
+  // (a zero gives M = 0 and X = 0 through the same arithmetic)
   unsigned long long M = be ? (f | (1ull << 52)) : f;
   int bee = be ? be : 1;
   int sh = bee - 1075 + 8 * S - 1 - e;
