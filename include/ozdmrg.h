@@ -213,8 +213,19 @@ typedef struct oz_heff_info {
   int slices, level, mode;
   int tile;               /* OZ_TILE_CTA or OZ_TILE_PAIR: the GEMM tiles of the products */
   int units;              /* persistent units of the GEMM launches: CTAs, or CTA pairs */
+  int epilogue1, epilogue2;/* epilogue layout of the stage-1 / stage-2 GEMM launches: 0 = 16 warps
+                              owning 16 columns each (short tiles), 1 = 8 owners of 32 columns with
+                              TMEM lane quarter 1 handed over by a loader warp, which keeps the MMA
+                              issuer's scheduler partition free (long tiles: 48 k-blocks or more on
+                              average); identical results.  Set once the handle has run its first
+                              product (or by oz_heff_set_epilogue), 0 before */
 } oz_heff_info;
 int oz_heff_info_get(const oz_heff* h, oz_heff_info* out);
+/* Epilogue layout of the stage-1 / stage-2 GEMM launches of an emulated handle (see
+ * oz_heff_info.epilogue1/2): 0, 1, or -1 for the automatic choice from the tile lengths.  Results
+ * are identical; re-captures the handle's graph (synchronises the device).  OZ_EINVAL for other
+ * values, native handles, or layout 1 on a CTA-pair handle. */
+int oz_heff_set_epilogue(oz_heff* h, int e1, int e2);
 /* Per-block precision dial (emulated handles): s1[q] = slice level of the stage-1 product of
  * source sector q, s2[q] = level of the stage-2 product of target sector q (arrays of nsec ints;
  * null = the handle's level).  Each level must lie in 1..the handle's level s; the operator and

@@ -175,6 +175,11 @@ class Heff:
         except Exception:
             pass
 
+    def set_epilogue(self, e1: int = -1, e2: int = -1):
+        """Epilogue layout of the stage-1 / stage-2 GEMM launches (0, 1, -1 = automatic); the results
+        are identical (``oz_heff_set_epilogue``)."""
+        N.check(self.lib.oz_heff_set_epilogue(self.h, int(e1), int(e2)))
+
     def info(self) -> dict:
         inf = N.oz_heff_info()
         N.check(self.lib.oz_heff_info_get(self.h, C.byref(inf)))

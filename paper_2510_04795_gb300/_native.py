@@ -39,7 +39,7 @@ class oz_heff_info(C.Structure):
     _fields_ = [("dim", C.c_longlong), ("flops", C.c_longlong), ("carrier_flops", C.c_longlong),
                 ("bytes_ops", C.c_longlong), ("bytes_scratch", C.c_longlong), ("gemm1_tiles", C.c_longlong),
                 ("gemm2_tiles", C.c_longlong), ("slices", C.c_int), ("level", C.c_int), ("mode", C.c_int),
-                ("tile", C.c_int), ("units", C.c_int)]
+                ("tile", C.c_int), ("units", C.c_int), ("epilogue1", C.c_int), ("epilogue2", C.c_int)]
 
 
 class oz_dmrg_step(C.Structure):
@@ -124,6 +124,7 @@ def load():
         "oz_heff_partition": (i, [i, vp, vp, i, vp, vp, i, vp]),
         "oz_heff_ops_times": (i, [vp, vp, vp]),
         "oz_reduce_ordered": (i, [vp, i, ll, vp, vp]),
+        "oz_heff_set_epilogue": (i, [vp, i, i]),
         "oz_heff_apply_streamed": (i, [vp, i, C.POINTER(i), C.POINTER(i), i, C.POINTER(oz_task), C.POINTER(oz_prec),
                                        i, vp, vp, vp]),
         "oz_dmrg_trace": (i, [vp, ll, vp, vp, vp, vp, C.POINTER(ll)]),

@@ -276,7 +276,8 @@ extern "C" int ozaki_gemm(oz_ctx* c, int m, int n, int k, double alpha, const do
   P.M = m; P.N = n; P.nkb = o.nkb; P.SA = S; P.SB = S; P.s = s;
   P.mode = oz::OUT_DENSE; P.C = C; P.ldc = ldc; P.alpha = alpha; P.beta = beta;
   int ntiles = o.nrbA * o.nrbB;
-  OZ_CU(oz::launch_gemm(nullptr, nullptr, ntiles, c->nsm, &P, 0, c->d_flags + 1, st));
+  OZ_CU(oz::launch_gemm(nullptr, nullptr, ntiles, c->nsm, &P, 0, c->d_flags + 1, st, nullptr, false,
+                        oz::gemm_handover_for(o.nkb)));
   return OZ_OK;
 }
 
@@ -352,12 +353,12 @@ int oz_heff_s::enqueue(cudaStream_t st, bool capturing) {
     OZ_CU(oz::launch_rowmax(dSegPsi, nullptr, nsegPsi, uPsiM, ctx->d_flags, st, dCtaPsiM));
     OZ_CU(oz::launch_digits(dSegPsi, nullptr, nsegPsi, uPsiD, S, st, dCtaPsiD));
     OZ_CU(cudaEventRecordWithFlags(ev[1], st, evf));
-    OZ_CU(oz::launch_gemm(dP1, dT1, nt1, units, nullptr, s, ctx->d_flags + 1, st, dF1, pair));
+    OZ_CU(oz::launch_gemm(dP1, dT1, nt1, units, nullptr, s, ctx->d_flags + 1, st, dF1, pair, ho1));
     OZ_CU(cudaEventRecordWithFlags(ev[2], st, evf));
     OZ_CU(oz::launch_digits(dSegA2, nullptr, nsegA2, uA2D, S, st, dCtaA2D));
     if (zero_y) OZ_CU(cudaMemsetAsync(dY, 0, (size_t)dim * 8, st));
     OZ_CU(cudaEventRecordWithFlags(ev[3], st, evf));
-    OZ_CU(oz::launch_gemm(dP2, dT2, nt2, units, nullptr, s, ctx->d_flags + 1, st, dF2, pair));
+    OZ_CU(oz::launch_gemm(dP2, dT2, nt2, units, nullptr, s, ctx->d_flags + 1, st, dF2, pair, ho2));
     OZ_CU(cudaEventRecordWithFlags(ev[4], st, evf));
     return OZ_OK;
   }
@@ -858,6 +859,14 @@ int oz_heff_s::prepare() {
     std::vector<GemmTile> t1 = make_tiles(p1), t2 = make_tiles(p2);
     this->nt1 = (int)t1.size();
     this->nt2 = (int)t2.size();
+    // epilogue layout per stage from the average tile length (CTA pairs: the 16-owner layout)
+    auto kb_per_tile = [](const std::vector<GemmProblem>& ps, const std::vector<GemmTile>& tl) {
+      double kb = 0.0;
+      for (const GemmTile& t : tl) kb += ps[t.prob].nkb;
+      return tl.empty() ? 0.0 : kb / (double)tl.size();
+    };
+    this->ho1 = this->ho1_auto = !this->pair && oz::gemm_handover_for(kb_per_tile(p1, t1));
+    this->ho2 = this->ho2_auto = !this->pair && oz::gemm_handover_for(kb_per_tile(p2, t2));
     this->bt1 = t1;
     this->bt2 = t2;
     if ((rc = this->alloc(&this->dF1, (size_t)(c->nsm + 1) * 4))) return rc;
@@ -921,23 +930,45 @@ int oz_heff_s::prepare() {
   }
   // ---- CUDA graph of one product (psi and y are the handle's own buffers)
   OZ_CU(cudaStreamCreateWithFlags(&this->cap, cudaStreamNonBlocking));
-  if (mode == OZ_MODE_EAGER) {
-    // warm launch outside capture sets kernel attributes once (on a zero psi: no stale NaN patterns)
-    OZ_CU(cudaMemset(this->dPsi, 0, (size_t)this->dim * 8));
-    if ((rc = this->enqueue(this->cap))) return rc;
-    OZ_CU(cudaStreamSynchronize(this->cap));
-    cudaGraph_t g;
-    OZ_CU(cudaStreamBeginCapture(this->cap, cudaStreamCaptureModeThreadLocal));
-    rc = this->enqueue(this->cap, true);
-    cudaError_t e = cudaStreamEndCapture(this->cap, &g);
-    if (rc) return rc;
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&this->exec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-  }
+  if (mode == OZ_MODE_EAGER && (rc = this->capture())) return rc;
   prepared = true;
   return OZ_OK;
+}
+
+// (Re)captures the graph of one product with the current launch configuration.
+int oz_heff_s::capture() {
+  if (exec) {
+    cudaGraphExecDestroy(exec);
+    exec = nullptr;
+  }
+  // warm launch outside capture sets kernel attributes once (on a zero psi: no stale NaN patterns)
+  OZ_CU(cudaMemset(this->dPsi, 0, (size_t)this->dim * 8));
+  if (int rc = this->enqueue(this->cap)) return rc;
+  OZ_CU(cudaStreamSynchronize(this->cap));
+  cudaGraph_t g;
+  OZ_CU(cudaStreamBeginCapture(this->cap, cudaStreamCaptureModeThreadLocal));
+  const int rc = this->enqueue(this->cap, true);
+  cudaError_t e = cudaStreamEndCapture(this->cap, &g);
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&this->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  return OZ_OK;
+}
+
+extern "C" int oz_heff_set_epilogue(oz_heff* h, int e1, int e2) {
+  if (!h) return fail(OZ_EINVAL, "handle is null");
+  if (h->mode != OZ_MODE_EAGER) return fail(OZ_EINVAL, "epilogue layouts exist for emulated handles only");
+  if (e1 < -1 || e1 > 1 || e2 < -1 || e2 > 1) return fail(OZ_EINVAL, "layouts are -1 (automatic), 0 or 1");
+  if (int rc = h->prepare()) return rc;
+  if (h->pair && (e1 == 1 || e2 == 1)) return fail(OZ_EINVAL, "CTA-pair handles use layout 0");
+  const bool n1 = e1 < 0 ? h->ho1_auto : e1 == 1, n2 = e2 < 0 ? h->ho2_auto : e2 == 1;
+  if (n1 == h->ho1 && n2 == h->ho2) return OZ_OK;
+  OZ_CU(cudaDeviceSynchronize());
+  h->ho1 = n1;
+  h->ho2 = n2;
+  return h->capture();
 }
 
 extern "C" int oz_heff_destroy(oz_heff* h) {
@@ -1019,6 +1050,8 @@ extern "C" int oz_heff_info_get(const oz_heff* h, oz_heff_info* o) {
   o->mode = h->mode;
   o->tile = h->pair ? OZ_TILE_PAIR : OZ_TILE_CTA;
   o->units = h->units;
+  o->epilogue1 = h->ho1 ? 1 : 0;
+  o->epilogue2 = h->ho2 ? 1 : 0;
   return OZ_OK;
 }
 

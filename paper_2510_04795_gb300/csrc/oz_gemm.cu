@@ -8,17 +8,20 @@
 // accumulator group holds at most GROUP_TERMS = 1008 products, so each FP32 partial sum is an
 // integer below 2^24 and the accumulation is exact (checked on the device against int64).
 //
-// One CTA per SM, persistent over a tile list; 18 warps:
+// One CTA per SM, persistent over a tile list; 12 warps, 3 per scheduler partition:
 //   warp 0       producer: cp.async.bulk of pre-tiled digit planes into a ring of shared-memory stages
 //   warp 1       TMEM owner and single-thread MMA issuer; diagonal g = t+u (0-based) of the slice
 //                grid accumulates into its own TMEM buffer (BN columns), A reused through the
 //                collector across the u loop; a buffer whose group is full is handed to the
 //                epilogue ("drain": one tcgen05.commit) and replaced by a free one
-//   warps 2..17  epilogue, 4 warps per TMEM lane quarter, 16 columns each: replays the same
-//                deterministic drain/buffer schedule, reads each drained buffer, adds
-//                q * 256^(s-1-g) into exact running sums per output element, then rounds once to
-//                FP64 scaled by 2^(ea+eb-8s-6), applies alpha/beta, stores (and for the row-table
-//                mode records a per-row |max| for the next slicing).
+//   epilogue     replays the same deterministic drain/buffer schedule.  Eight owners of exact running
+//                sums (32 columns of 32 rows each) read each drained buffer, add q * 256^(s-1-g)
+//                into their sums, then round once to FP64 scaled by 2^(ea+eb-8s-6), apply
+//                alpha/beta, store (and for the row-table mode record a per-row |max| for the next
+//                slicing).  A warp may read only the TMEM lane quarter of its partition, and the
+//                issuer's partition is kept free of the exact arithmetic: there warp 5 only loads
+//                lane quarter 1 and hands it to its two owners on partitions 2 and 3 through
+//                shared memory (warp 9 idles).
 // CTA pairs (gemm_kernel<true>, clusters of two CTAs on two SMs): one tile is 256 x 64; each CTA
 // loads its own 128 A rows and one 32-row half of the 64 B^T rows (the operand stores the halves of
 // each k-block apart), the first CTA's thread issues cta_group::2 MMAs of M = 256 for both (each CTA
@@ -44,34 +47,51 @@ namespace oz {
 
 constexpr int A_TILE_BYTES = TILE_M * KB * 2;             // 4 KB per plane
 constexpr int B_TILE_BYTES = BN * KB * 2;                 // 2 KB per plane
-constexpr int PLANE_BYTES = A_TILE_BYTES + B_TILE_BYTES;  // one slice plane of A and of B^T per k-block
 constexpr int BH_BYTES = B_TILE_BYTES / 2;                // a CTA pair: each CTA's half (32 rows) of a B^T plane
 __host__ __device__ constexpr int plane_bytes(bool pair) { return A_TILE_BYTES + (pair ? BH_BYTES : B_TILE_BYTES); }
-constexpr int EPI_WARPS = 16;
-constexpr int CW = BN / (EPI_WARPS / 4);                  // columns per epilogue warp (16)
-constexpr int NTHREADS = 32 * (2 + EPI_WARPS);
 constexpr int MAX_STAGES = 4;
-// Final-stage staging: per epilogue warp, 32 rows x ZC columns of 16-byte exact sums (converted in
+constexpr int HO_SLOTS = 4;                               // hand-over slots of lane quarter 1
+constexpr int HO_BYTES = HO_SLOTS * 32 * BN * 4;
+// Final-stage staging: per owner warp, 32 rows x ZC columns of 16-byte exact sums (converted in
 // place to doubles); row stride (ZC + 1) x 16 bytes against bank conflicts.
 constexpr int ZC = 4;
 constexpr int ZS_LD = ZC + 1;
-constexpr int ZS_BYTES = EPI_WARPS * 32 * ZS_LD * 16;
+// Two epilogue layouts, chosen per launch (a warp runs on scheduler partition warp % 4 and may read
+// only TMEM lane quarter warp % 4):
+//  * HO = false: 18 warps -- 0 producer, 1 MMA issuer, 2..17 owners of the exact sums, four per lane
+//    quarter with 16 columns each.  Many owners keep the final conversion of short tiles fast.
+//  * HO = true: 12 warps, 3 per partition -- 0 producer, 1 issuer; owners of 32 columns: quarter 0:
+//    4, 8; quarter 2: 2, 6; quarter 3: 3, 7; quarter 1: 10, 11 (partitions 2 and 3), fed by warp 5,
+//    the loader of lane quarter 1, which reads the drained buffer's lanes 32..63 and hands them over
+//    through shared memory, so that the issuer's partition runs no exact arithmetic; warp 9 idles.
+//    Drain-heavy long tiles run faster this way.
+template <bool HO>
+struct EpiCfg {
+  static constexpr int NWARPS = HO ? 12 : 18;
+  static constexpr int NTHREADS = 32 * NWARPS;
+  static constexpr int OWNERS = HO ? 8 : 16;              // warps holding exact sums
+  static constexpr int CW = BN / (HO ? 2 : 4);            // columns per owner
+  static constexpr int READERS = HO ? 7 : 16;             // warps reading TMEM per drain
+  static constexpr int ZS_BYTES = OWNERS * 32 * ZS_LD * 16 + (HO ? HO_BYTES : 0);
+};
 constexpr int SMEM_LIMIT = 232448;                        // opt-in shared memory per block
 
 struct Shared {
   unsigned long long full[MAX_STAGES], empty[MAX_STAGES], accf[NBUF], acce[NBUF], fin;
+  unsigned long long hfull[HO_SLOTS], hempty[HO_SLOTS];  // quarter-1 hand-over: loader -> owners 10, 11
   uint32_t tmem;
   int abort;
 };
 
 // pipeline stages that fit next to the staging area for slice level smax
-int gemm_stages(int smax, bool pair) {
-  const int avail = SMEM_LIMIT - ZS_BYTES - (int)sizeof(Shared) - 1024;
+static int zs_bytes(bool ho) { return ho ? EpiCfg<true>::ZS_BYTES : EpiCfg<false>::ZS_BYTES; }
+int gemm_stages(int smax, bool pair, bool ho) {
+  const int avail = SMEM_LIMIT - zs_bytes(ho) - (int)sizeof(Shared) - 1024;
   const int n = avail / (smax * plane_bytes(pair));
   return n < MAX_STAGES ? n : MAX_STAGES;
 }
-size_t gemm_smem_bytes(int smax, bool pair) {
-  return (size_t)gemm_stages(smax, pair) * smax * plane_bytes(pair) + ZS_BYTES + sizeof(Shared) + 1024;
+size_t gemm_smem_bytes(int smax, bool pair, bool ho) {
+  return (size_t)gemm_stages(smax, pair, ho) * smax * plane_bytes(pair) + zs_bytes(ho) + sizeof(Shared) + 1024;
 }
 
 __device__ __forceinline__ uint32_t bar(const unsigned long long* p) { return smem_u32(p); }
@@ -260,24 +280,54 @@ __device__ void mma_last_diagonal(Shared& sh, MmaCtl& c, uint32_t tmem, uint32_t
   post<PAIR>(sh, c, buf);
 }
 
-// Epilogue side of one drain: wait until the MMAs into buffer b are complete, read this warp's
-// 32 x CW slice, release the buffer, add q * 2^shl into the exact running sums (one 96-bit
-// two's-complement integer w2:w1:w0 per output element).
+// a warp's 32 TMEM lanes x 16 or 32 columns
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&r)[16]) { tmem_ld16(taddr, r); }
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&r)[32]) { tmem_ld32(taddr, r); }
+
+// Epilogue roles of the drains (see the epilogue layouts above)
+enum : int { ROLE_TMEM_OWNER = 0, ROLE_LOADER = 1, ROLE_HO_OWNER = 2 };
+
+// Epilogue side of one drain of buffer b:
+//  * a TMEM owner waits until the MMAs into the buffer are complete, reads its 32 lanes x CW
+//    columns, releases the buffer and adds q * 2^shl into its exact running sums (one 96-bit
+//    two's-complement integer z2:z1:z0 per output element);
+//  * a quarter-1 owner takes its 32 columns from the loader's hand-over slot instead, frees it, and
+//    adds in the same way (drain_load below is the loader's side).
+// Slots are used in drain order by the loader and both quarter-1 owners (hcount counts drains).
 // (In a CTA pair the buffer is released on the first CTA's barrier, where the issuer waits for it.)
-__device__ __forceinline__ bool drain_into(Shared& sh, uint32_t tmem, int lq, int cg, int lane, uint32_t b, int shl,
-                                           uint32_t& accf_par, volatile int* abort, uint32_t (&z0)[CW],
-                                           uint32_t (&z1)[CW], uint32_t (&z2)[CW], bool remote_release) {
-  if (!mbar_wait(bar(&sh.accf[b]), (accf_par >> b) & 1u, abort)) return false;
-  accf_par ^= 1u << b;
-  tc_fence_after();
+template <int CW>
+__device__ __forceinline__ bool drain_into(Shared& sh, const float4* ho, int role, uint32_t tmem, int lq, int cg,
+                                           int lane, uint32_t b, int shl, uint32_t& accf_par, uint32_t& hcount,
+                                           volatile int* abort, uint32_t (&z0)[CW], uint32_t (&z1)[CW],
+                                           uint32_t (&z2)[CW], bool remote_release) {
   uint32_t v[CW];
-  tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + b * BN + cg * CW, v);
-  tmem_wait_ld();
-  tc_fence_before();
-  __syncwarp();
-  if (lane == 0) {
-    if (remote_release) mbar_arrive_remote(mapa_shared(bar(&sh.acce[b]), 0));
-    else mbar_arrive(bar(&sh.acce[b]));
+  if (role == ROLE_TMEM_OWNER) {
+    if (!mbar_wait(bar(&sh.accf[b]), (accf_par >> b) & 1u, abort)) return false;
+    accf_par ^= 1u << b;
+    tc_fence_after();
+    tmem_ld_cols(tmem + ((uint32_t)(lq * 32) << 16) + b * BN + cg * CW, v);
+    tmem_wait_ld();
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) {
+      if (remote_release) mbar_arrive_remote(mapa_shared(bar(&sh.acce[b]), 0));
+      else mbar_arrive(bar(&sh.acce[b]));
+    }
+  } else {
+    const uint32_t slot = hcount % HO_SLOTS, ph = (hcount / HO_SLOTS) & 1u;
+    ++hcount;
+    if (!mbar_wait(bar(&sh.hfull[slot]), ph, abort)) return false;
+    const float4* hs = ho + slot * (BN / 4) * 32 + cg * (CW / 4) * 32;
+#pragma unroll
+    for (int c = 0; c < CW / 4; ++c) {
+      const float4 f = hs[c * 32 + lane];
+      v[4 * c] = __float_as_uint(f.x);
+      v[4 * c + 1] = __float_as_uint(f.y);
+      v[4 * c + 2] = __float_as_uint(f.z);
+      v[4 * c + 3] = __float_as_uint(f.w);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(bar(&sh.hempty[slot]));
   }
   if (shl >= 64) {
     // level 9, diagonal 0: weight 2^64, the top word alone (the sums are kept modulo 2^96)
@@ -288,6 +338,81 @@ __device__ __forceinline__ bool drain_into(Shared& sh, uint32_t tmem, int lq, in
 #pragma unroll
   for (int j = 0; j < CW; ++j) w96_add_shifted(z0[j], z1[j], z2[j], __float2int_rn(__uint_as_float(v[j])), shl);
   return true;
+}
+
+// The loader's side of one drain: lanes 32..63 of buffer b, all 64 columns, read and released, then
+// written to the next hand-over slot ([slot][column / 4][lane][4] floats) once both quarter-1 owners
+// have taken its previous contents.
+__device__ __forceinline__ bool drain_load(Shared& sh, float4* ho, uint32_t tmem, int lane, uint32_t b,
+                                           uint32_t& accf_par, uint32_t& hcount, volatile int* abort,
+                                           bool remote_release) {
+  if (!mbar_wait(bar(&sh.accf[b]), (accf_par >> b) & 1u, abort)) return false;
+  accf_par ^= 1u << b;
+  tc_fence_after();
+  constexpr int CW = BN / 2;  // the two halves of the 64 columns
+  uint32_t v[CW], u[CW];
+  tmem_ld32(tmem + (32u << 16) + b * BN, v);
+  tmem_ld32(tmem + (32u << 16) + b * BN + CW, u);
+  tmem_wait_ld();
+  tc_fence_before();
+  __syncwarp();
+  if (lane == 0) {
+    if (remote_release) mbar_arrive_remote(mapa_shared(bar(&sh.acce[b]), 0));
+    else mbar_arrive(bar(&sh.acce[b]));
+  }
+  const uint32_t slot = hcount % HO_SLOTS, ph = (hcount / HO_SLOTS) & 1u;
+  ++hcount;
+  if (!mbar_wait(bar(&sh.hempty[slot]), ph ^ 1u, abort)) return false;
+  float4* hs = ho + slot * (BN / 4) * 32;
+#pragma unroll
+  for (int c = 0; c < CW / 4; ++c) {
+    hs[c * 32 + lane] = make_float4(__uint_as_float(v[4 * c]), __uint_as_float(v[4 * c + 1]),
+                                    __uint_as_float(v[4 * c + 2]), __uint_as_float(v[4 * c + 3]));
+    hs[(CW / 4 + c) * 32 + lane] = make_float4(__uint_as_float(u[4 * c]), __uint_as_float(u[4 * c + 1]),
+                                               __uint_as_float(u[4 * c + 2]), __uint_as_float(u[4 * c + 3]));
+  }
+  __syncwarp();
+  if (lane == 0) mbar_arrive(bar(&sh.hfull[slot]));
+  return true;
+}
+
+// The drain schedule of one tile, replayed in the issuer's order: the buffers of k-block 0, then
+// the mid-tile drains ordered by (k-block, diagonal), then the final buffers; drain(b, shl) handles
+// buffer b whose diagonal carries the weight 2^shl.  Level 9: the first pass takes diagonals 0..7
+// on the level-8 plan, the second diagonal 8 alone, drained every LAST_PERIOD k-blocks.
+template <typename F>
+__device__ __forceinline__ bool replay_drains(int S, int nkb, BufRing& er, F&& drain) {
+  const bool stag = stagger_of(nkb);
+  uint32_t bufs[SPLIT_LEVEL - 1];  // a pass has at most 8 diagonals
+  int nxt[SPLIT_LEVEL - 1], per[SPLIT_LEVEL - 1];
+  bool ok = true;
+  for (int pass = 0; pass < passes_of(S) && ok; ++pass) {
+    const int g0 = pass ? SPLIT_LEVEL - 1 : 0;                 // first diagonal of the pass
+    const int nd = pass ? 1 : (S == SPLIT_LEVEL ? S - 1 : S);  // its diagonals
+    for (int d = nd - 1; d >= 0; --d) bufs[d] = er.next();
+    for (int d = 0; d < nd; ++d) {
+      if (pass) nxt[d] = per[d] = LAST_PERIOD;
+      else drain_plan(d, nd, stag, nxt[d], per[d]);
+    }
+    while (ok) {
+      int kbmin = nkb, dsel = -1;
+      for (int d = 0; d < nd; ++d)
+        if (nxt[d] < kbmin) {
+          kbmin = nxt[d];
+          dsel = d;
+        }
+      if (dsel < 0) break;
+      ok = drain(bufs[dsel], 8 * (S - 1 - g0 - dsel));
+      er.posted(bufs[dsel]);
+      bufs[dsel] = er.next();
+      nxt[dsel] += per[dsel];
+    }
+    for (int d = 0; d < nd && ok; ++d) {
+      ok = drain(bufs[d], 8 * (S - 1 - g0 - d));
+      er.posted(bufs[d]);
+    }
+  }
+  return ok;
 }
 
 __device__ __forceinline__ void tile_of(const GemmTile* tiles, const GemmProblem* probs, const GemmProblem& single,
@@ -305,17 +430,19 @@ __device__ __forceinline__ void tile_of(const GemmTile* tiles, const GemmProblem
   }
 }
 
-template <bool PAIR>
-__global__ void __launch_bounds__(NTHREADS, 1)
+template <bool PAIR, bool HO>
+__global__ void __launch_bounds__(EpiCfg<HO>::NTHREADS, 1)
     gemm_kernel(const GemmProblem* __restrict__ probs, const GemmTile* __restrict__ tiles, int ntiles,
                 const int* __restrict__ first,
                 const __grid_constant__ GemmProblem single, int smax, int nstage, int* __restrict__ err) {
+  using E = EpiCfg<HO>;
+  constexpr int CW = E::CW;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr int BPL = PAIR ? BH_BYTES : B_TILE_BYTES;  // bytes of one B^T plane in a stage
   const uint32_t stage_bytes = (uint32_t)(smax * plane_bytes(PAIR)), boff = (uint32_t)(smax * A_TILE_BYTES);
   longlong2* zstage = reinterpret_cast<longlong2*>(smem + nstage * stage_bytes);
-  Shared& sh = *reinterpret_cast<Shared*>(smem + nstage * stage_bytes + ZS_BYTES);
+  Shared& sh = *reinterpret_cast<Shared*>(smem + nstage * stage_bytes + E::ZS_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* abort = &sh.abort;
   const uint32_t stage0 = smem_u32(smem);
@@ -331,9 +458,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     for (int i = 0; i < NBUF; ++i) {
       mbar_init(bar(&sh.accf[i]), 1);
-      mbar_init(bar(&sh.acce[i]), PAIR ? 2 * EPI_WARPS : EPI_WARPS);
+      mbar_init(bar(&sh.acce[i]), PAIR ? 2 * E::READERS : E::READERS);
     }
     mbar_init(bar(&sh.fin), 1);
+    for (int i = 0; i < HO_SLOTS; ++i) {
+      mbar_init(bar(&sh.hfull[i]), 1);
+      mbar_init(bar(&sh.hempty[i]), 2);
+    }
     sh.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -453,20 +584,39 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (stop) break;
       }
     }
-  } else {
-    // ------------------------------------------------------------------ epilogue
-    const int lq = warp & 3;              // TMEM lane quarter this warp may access
-    const int cg = (warp - 2) >> 2;       // column group of the BN-wide tile
-    uint32_t accf_par = 0;
+  } else if (HO && warp == 5) {
+    // ------------------------------------------------------------------ loader of lane quarter 1
+    uint32_t accf_par = 0, hcount = 0;
     BufRing er{0u, 0, 0};
-    longlong2* zs = zstage + (warp - 2) * 32 * ZS_LD;
+    float4* ho = reinterpret_cast<float4*>(zstage + E::OWNERS * 32 * ZS_LD);
+    for (int idx = it0; idx < it1 && !*abort; idx += istep) {
+      const GemmProblem* P;
+      int mb, nb;
+      tile_of(tiles, probs, single, idx, P, mb, nb);
+      if (!replay_drains(P->s, P->nkb, er, [&](uint32_t b, int) {
+            return drain_load(sh, ho, tmem, lane, b, accf_par, hcount, abort, PAIR && !lead);
+          }))
+        break;
+    }
+  } else if (!HO || warp != 9) {
+    // ------------------------------------------------------------------ owners of the exact sums
+    const int role = HO && warp >= 10 ? ROLE_HO_OWNER : ROLE_TMEM_OWNER;
+    const int lq = warp & 3;                               // TMEM lane quarter this warp may read
+    const int rq = role == ROLE_HO_OWNER ? 1 : lq;         // lane quarter (rows) of its exact sums
+    const int cg = role == ROLE_HO_OWNER ? warp - 10 : (warp - 2) >> 2;  // column group of the tile
+    // owner index (staging area): HO: 2, 3, 4, 6, 7, 8, 10, 11 -> 0..7; else warp - 2
+    const int oi = !HO ? warp - 2 : (role == ROLE_HO_OWNER ? warp - 4 : (warp < 5 ? warp - 2 : warp - 3));
+    uint32_t accf_par = 0, hcount = 0;
+    BufRing er{0u, 0, 0};
+    longlong2* zs = zstage + oi * 32 * ZS_LD;
+    const float4* ho = reinterpret_cast<const float4*>(zstage + E::OWNERS * 32 * ZS_LD);
     for (int idx = it0; idx < it1 && !*abort; idx += istep) {
       const GemmProblem* P;
       int mb, nb;
       tile_of(tiles, probs, single, idx, P, mb, nb);
       // per-tile operands of the final stage, loaded now so that their latency hides behind the drains
       const int M = P->M, N = P->N, mode = P->mode;
-      const int row = (PAIR ? 2 * mb + (int)rank : mb) * TILE_M + lq * 32 + lane;
+      const int row = (PAIR ? 2 * mb + (int)rank : mb) * TILE_M + rq * 32 + lane;
       const bool rowok = row < M;
       const int col0 = nb * BN + cg * CW;
       const int ebl = (lane < CW && col0 + lane < N) ? __ldg(P->eb + col0 + lane) : 0;
@@ -488,43 +638,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         z1[j] = 0u;
         z2[j] = 0u;
       }
-      bool ok = true;
-      // replay the issuer's schedule, pass by pass: the buffers of k-block 0, then the mid-tile
-      // drains ordered by (k-block, diagonal), then the final buffers.  Diagonal g carries the
-      // weight 256^(S-1-g).  Level 9: the first pass takes diagonals 0..7 on the level-8 plan, the
-      // second diagonal 8 alone, drained every LAST_PERIOD k-blocks.
-      const int S = P->s, nkb = P->nkb;
-      const bool stag = stagger_of(nkb);
-      uint32_t bufs[SPLIT_LEVEL - 1];  // a pass has at most 8 diagonals
-      int nxt[SPLIT_LEVEL - 1], per[SPLIT_LEVEL - 1];
-      for (int pass = 0; pass < passes_of(S) && ok; ++pass) {
-        const int g0 = pass ? SPLIT_LEVEL - 1 : 0;                 // first diagonal of the pass
-        const int nd = pass ? 1 : (S == SPLIT_LEVEL ? S - 1 : S);  // its diagonals
-        for (int d = nd - 1; d >= 0; --d) bufs[d] = er.next();
-        for (int d = 0; d < nd; ++d) {
-          if (pass) nxt[d] = per[d] = LAST_PERIOD;
-          else drain_plan(d, nd, stag, nxt[d], per[d]);
-        }
-        while (ok) {
-          int kbmin = nkb, dsel = -1;
-          for (int d = 0; d < nd; ++d)
-            if (nxt[d] < kbmin) {
-              kbmin = nxt[d];
-              dsel = d;
-            }
-          if (dsel < 0) break;
-          ok = drain_into(sh, tmem, lq, cg, lane, bufs[dsel], 8 * (S - 1 - g0 - dsel), accf_par, abort, z0, z1, z2,
+      const int S = P->s;
+      const bool ok = replay_drains(S, P->nkb, er, [&](uint32_t b, int shl) {
+        return drain_into(sh, ho, role, tmem, lq, cg, lane, b, shl, accf_par, hcount, abort, z0, z1, z2,
                           PAIR && !lead);
-          er.posted(bufs[dsel]);
-          bufs[dsel] = er.next();
-          nxt[dsel] += per[dsel];
-        }
-        for (int d = 0; d < nd && ok; ++d) {
-          ok = drain_into(sh, tmem, lq, cg, lane, bufs[d], 8 * (S - 1 - g0 - d), accf_par, abort, z0, z1, z2,
-                          PAIR && !lead);
-          er.posted(bufs[d]);
-        }
-      }
+      });
       if (!ok) break;
       // ---- one rounding to FP64, scaling; the exact sums pass through shared memory ZC columns at a
       //      time so that the conversion code exists once (compact loop), and the stores are coalesced
@@ -656,7 +774,7 @@ namespace {
 // The shared-memory opt-in of a kernel belongs to the current device's context: record it per
 // device ordinal (bit d of a process-wide mask).  Setting it twice is harmless, so two host threads
 // racing on the same device need no lock.
-template <bool PAIR>
+template <bool PAIR, bool HO>
 cudaError_t opt_in_smem() {
   static std::atomic<unsigned long long> attr_set{0ull};
   int dev = 0;
@@ -664,7 +782,7 @@ cudaError_t opt_in_smem() {
   if (e != cudaSuccess) return e;
   const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
   if (!bit || !(attr_set.load(std::memory_order_acquire) & bit)) {
-    e = cudaFuncSetAttribute(gemm_kernel<PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
+    e = cudaFuncSetAttribute(gemm_kernel<PAIR, HO>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
     if (e != cudaSuccess) return e;
     attr_set.fetch_or(bit, std::memory_order_release);
   }
@@ -674,7 +792,7 @@ cudaError_t opt_in_smem() {
 
 int gemm_pair_units(int nsm) {
   // CTA pairs that run at the same time on the current device (clusters of 2, one CTA per SM)
-  if (opt_in_smem<true>() != cudaSuccess) return 0;
+  if (opt_in_smem<true, false>() != cudaSuccess) return 0;
   cudaLaunchConfig_t cfg{};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -682,12 +800,12 @@ int gemm_pair_units(int nsm) {
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3((unsigned)(nsm / 2 * 2), 1, 1);
-  cfg.blockDim = dim3(NTHREADS, 1, 1);
-  cfg.dynamicSmemBytes = gemm_smem_bytes(MAX_LEVEL, true);
+  cfg.blockDim = dim3(EpiCfg<false>::NTHREADS, 1, 1);
+  cfg.dynamicSmemBytes = gemm_smem_bytes(MAX_LEVEL, true, false);
   cfg.attrs = at;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, gemm_kernel<true>, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&n, gemm_kernel<true, false>, &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -696,9 +814,10 @@ int gemm_pair_units(int nsm) {
 
 cudaError_t launch_gemm(const GemmProblem* d_probs, const GemmTile* d_tiles, int ntiles, int grid,
                         const GemmProblem* single, int smax, int* d_err, cudaStream_t st, const int* d_first,
-                        bool pair) {
+                        bool pair, bool ho) {
   if (ntiles <= 0) return cudaSuccess;
-  cudaError_t e = pair ? opt_in_smem<true>() : opt_in_smem<false>();
+  if (pair) ho = false;  // CTA pairs keep the 18-warp layout
+  cudaError_t e = pair ? opt_in_smem<true, false>() : (ho ? opt_in_smem<false, true>() : opt_in_smem<false, false>());
   if (e != cudaSuccess) return e;
   GemmProblem one{};
   if (single) {
@@ -706,11 +825,15 @@ cudaError_t launch_gemm(const GemmProblem* d_probs, const GemmTile* d_tiles, int
     smax = one.s;
   }
   if (smax < 1 || smax > MAX_LEVEL) return cudaErrorInvalidValue;
-  const int nstage = gemm_stages(smax, pair);
+  const int nstage = gemm_stages(smax, pair, ho);
   const int g = d_first ? grid : (grid < ntiles ? grid : ntiles);
   if (!pair) {
-    gemm_kernel<false><<<g, NTHREADS, gemm_smem_bytes(smax, false), st>>>(d_probs, d_tiles, ntiles, d_first, one, smax,
-                                                                         nstage, d_err);
+    if (ho)
+      gemm_kernel<false, true><<<g, EpiCfg<true>::NTHREADS, gemm_smem_bytes(smax, false, true), st>>>(
+          d_probs, d_tiles, ntiles, d_first, one, smax, nstage, d_err);
+    else
+      gemm_kernel<false, false><<<g, EpiCfg<false>::NTHREADS, gemm_smem_bytes(smax, false, false), st>>>(
+          d_probs, d_tiles, ntiles, d_first, one, smax, nstage, d_err);
     return cudaGetLastError();
   }
   // g CTA pairs: clusters of two CTAs on two SMs
@@ -721,12 +844,13 @@ cudaError_t launch_gemm(const GemmProblem* d_probs, const GemmTile* d_tiles, int
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3((unsigned)(2 * g), 1, 1);
-  cfg.blockDim = dim3(NTHREADS, 1, 1);
-  cfg.dynamicSmemBytes = gemm_smem_bytes(smax, true);
+  cfg.blockDim = dim3(EpiCfg<false>::NTHREADS, 1, 1);
+  cfg.dynamicSmemBytes = gemm_smem_bytes(smax, true, false);
   cfg.stream = st;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, gemm_kernel<true>, d_probs, d_tiles, ntiles, d_first, one, smax, nstage, d_err);
+  return cudaLaunchKernelEx(&cfg, gemm_kernel<true, false>, d_probs, d_tiles, ntiles, d_first, one, smax, nstage,
+                            d_err);
 }
 
 }  // namespace oz

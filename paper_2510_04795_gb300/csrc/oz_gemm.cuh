@@ -49,17 +49,22 @@ struct GemmTile {
   int prob, mb, nb, pad;
 };
 
-size_t gemm_smem_bytes(int smax, bool pair);
+size_t gemm_smem_bytes(int smax, bool pair, bool ho = false);
 // tiles == nullptr: a single problem (*single) with implicit tiles i -> (i / nnb, i % nnb);
 // otherwise smax is the largest slice level among the launch's problems (sizes the pipeline stages).
 // d_first (grid + 1 entries, optional): unit b processes tiles [d_first[b], d_first[b+1]) in order;
 // without it unit b takes tiles b, b + grid, ...  A unit is one CTA, or with pair = true a CTA pair
 // (cluster of two CTAs on two SMs) computing 256 x 64 tiles: tile.mb then counts 256-row blocks, and
 // every B^T operand must store the two 32-row halves of each k-block of a 64-row tile one after the
-// other (SliceSeg::half_major).
+// other (SliceSeg::half_major).  ho selects the epilogue layout: false, 16 owner warps of 16 columns
+// (short tiles: fast final conversion); true, 8 owners of 32 columns with lane quarter 1 handed over
+// by a loader warp so that the MMA issuer's scheduler partition runs no exact arithmetic (long,
+// drain-heavy tiles).  Results are identical.  CTA pairs use the first.
 cudaError_t launch_gemm(const GemmProblem* d_probs, const GemmTile* d_tiles, int ntiles, int grid,
                         const GemmProblem* single, int smax, int* d_err, cudaStream_t st,
-                        const int* d_first = nullptr, bool pair = false);
+                        const int* d_first = nullptr, bool pair = false, bool ho = false);
+// The epilogue layout for a launch whose tiles average `kb_per_tile` k-blocks.
+inline bool gemm_handover_for(double kb_per_tile) { return kb_per_tile >= 48.0; }
 // CTA pairs that can run concurrently on the current device for `nsm` SMs (0: none).
 int gemm_pair_units(int nsm);
 // Balanced assignment of a tile list to `grid` CTAs (longest processing time first, cost of a

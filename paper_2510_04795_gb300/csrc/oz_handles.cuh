@@ -96,6 +96,8 @@ struct oz_heff_s {
   std::vector<oz::GemmTile> ht1, ht2;  // the same, scheduled over the CTAs (uploaded)
   int *dF1 = nullptr, *dF2 = nullptr;  // per-CTA first tile of each stage (nsm + 1 entries)
   int sched1 = 0, sched2 = 0;          // schedule of each stage (oz::SCHED_*), set by the autotuner
+  bool ho1 = false, ho2 = false;  // epilogue layouts of the two GEMM launches (hand-over of lane quarter 1)
+  bool ho1_auto = false, ho2_auto = false;  // the layouts chosen from the tile lengths
   bool pair = false;                   // products on CTA pairs (256 x 64 tiles)
   int units = 0;                       // persistent units of the GEMM launches: CTAs, or CTA pairs
   int balance();                       // (re)assigns the tiles to CTAs for the current levels
@@ -124,4 +126,5 @@ struct oz_heff_s {
     return OZ_OK;
   }
   int enqueue(cudaStream_t st, bool capturing = false);
+  int capture();
 };

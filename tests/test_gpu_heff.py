@@ -49,6 +49,30 @@ def test_heff_bitexact_vs_emulated_oracle(ctx, seed, grid, dims, S, s, tile):
     h.close()
 
 
+def test_heff_epilogue_layouts_bitexact(ctx):
+    """Both epilogue layouts of the GEMM launches (16 owner warps; 8 owners with TMEM lane quarter 1
+    handed over by a loader warp), in every combination over the two stages, give the oracle's bits;
+    the automatic choice takes the hand-over layout for long tiles only."""
+    import paper_2510_04795_gb300 as oz
+    st, blocks, psi = _problem((4, 4), (30, 300), 8, True, 4)
+    h = oz.Heff(ctx, st.m, st.n, _tasks(st, blocks), slices=7)
+    Lb = [b[0].cpu().numpy() for b in blocks]
+    Rb = [b[1].cpu().numpy() for b in blocks]
+    ref = heff.heff_apply_emulated(st, Lb, Rb, psi.cpu().numpy(), 7)
+    for e1 in (0, 1):
+        for e2 in (0, 1):
+            h.set_epilogue(e1, e2)
+            inf = h.info()
+            assert (inf["epilogue1"], inf["epilogue2"]) == (e1, e2)
+            y = h.apply(psi)
+            ctx.status()
+            assert np.array_equal(y.cpu().numpy().view(np.int64), ref.view(np.int64)), (e1, e2)
+    h.set_epilogue(-1, -1)
+    with pytest.raises(oz.OzError):
+        h.set_epilogue(2, 0)
+    h.close()
+
+
 def test_heff_repeatable_and_graph_replay(ctx):
     import paper_2510_04795_gb300 as oz
     st, blocks, psi = _problem((4, 4), (4, 60), 16, True, 5)
