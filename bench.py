@@ -29,8 +29,8 @@ FALLBACK_PEAK = {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gb
 
 # DRAM bytes per algorithmic carrier flop of the GEMM kernel, from one ncu capture, and the
 # digest of the kernel source it was taken on (the figure is dropped once the source changes).
-NCU_TRAFFIC = {"bytes_per_carrier_flop": 0.0021576,
-               "gemm_source_sha256": "0e0a4d645c357bc194948dbb1034c28963c7539a38d11ef7911d8ada3bb4d668"}
+NCU_TRAFFIC = {"bytes_per_carrier_flop": 0.0021499,
+               "gemm_source_sha256": "22ba91db7cd4e05c7402ede2125e20fc02b9c82b1278585d2dcc7f841427ce12"}
 
 
 def parse():
@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--no-learned", action="store_true", help="skip training and timing the learned level selector")
     p.add_argument("--no-shapes", action="store_true", help="skip timing the CTA-pair tile shape")
     p.add_argument("--no-epilogues", action="store_true", help="skip timing the two epilogue layouts")
+    p.add_argument("--epilogue", type=int, default=-1, choices=[-1, 0, 1],
+                   help="epilogue layout of both GEMM launches of the timed handle (-1: the automatic choice)")
     p.add_argument("--learned-structures", type=int, default=3)
     p.add_argument("--no-select", action="store_true",
                    help="skip the informational per-block-level run (analytic selector, 1e-12 budget)")
@@ -451,6 +453,8 @@ def main():
 
     h = oz.Heff(ctx, st.m, st.n, tasks, slices=S)
     ops_ms, ops_bytes = oz.heff_ops_times(h)
+    if args.epilogue >= 0:
+        h.set_epilogue(args.epilogue, args.epilogue)
     del tasks, Lbuf, Rbuf
     torch.cuda.empty_cache()
     tuned = None
@@ -516,7 +520,7 @@ def main():
                     acc[i] += v
             same = same and bool(torch.equal(y2, y))
             epilogues[f"layout{e}"] = {"gemm_stage1_ms": acc[1] / 3, "gemm_stage2_ms": acc[3] / 3}
-        h.set_epilogue(-1, -1)
+        h.set_epilogue(args.epilogue, args.epilogue)
         epilogues["results_equal"] = same
         del y2
         ctx.status()
