@@ -197,3 +197,21 @@ def test_integer_fixed_point_equals_fraction_definition(S):
     D_ref = ozaki.digits(X_ref, S)
     D = ozaki.digits_int(X, S)
     assert all(np.array_equal(a, b) for a, b in zip(D, D_ref))
+
+
+def test_level9_largest_sum_closed_form():
+    """Every value 127/128 is its own row maximum (e = 0) and has the fixed point 127 * 256^8: one
+    leading digit 127, all others zero.  At level 9 the exact sum of an output is then
+    K * 127^2 * 256^8 (the largest sum the emulated product can meet for a given K), and the
+    result is K (127/128)^2 exactly."""
+    K = 64
+    A = np.full((2, K), 127.0 / 128.0)
+    B = np.full((K, 3), -127.0 / 128.0)
+    e, D = ozaki.slice_rows(A, 9)
+    assert np.all(e == 0)
+    assert np.all(D[0] == 127) and all(np.all(d == 0) for d in D[1:])
+    C = ozaki.ozaki_gemm(A, B, 9, 9)
+    assert np.all(C == -K * (127.0 / 128.0) ** 2)
+    # the weight of the leading pair at level 9 is 256^(2*9 - 2) / 2^(2(8*9-1)) relative to 2^(ea+eb)
+    Z = K * 127 * (-127) * 256 ** (2 * 9 - 2)
+    assert ozaki.round_scaled(Z, -2 * (8 * 9 - 1)) == C[0, 0]
