@@ -29,8 +29,8 @@ FALLBACK_PEAK = {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gb
 
 # DRAM bytes per algorithmic carrier flop of the GEMM kernel, from one ncu capture, and the
 # digest of the kernel source it was taken on (the figure is dropped once the source changes).
-NCU_TRAFFIC = {"bytes_per_carrier_flop": 0.0021499,
-               "gemm_source_sha256": "22ba91db7cd4e05c7402ede2125e20fc02b9c82b1278585d2dcc7f841427ce12"}
+NCU_TRAFFIC = {"bytes_per_carrier_flop": 0.0021509,
+               "gemm_source_sha256": "34a8df24c12ec5bb350dc7c01d8048bb861b11ce80b01bedc5c6798e5ce5e1c9"}
 
 
 def parse():

@@ -8,21 +8,20 @@
 // accumulator group holds at most GROUP_TERMS = 1008 products, so each FP32 partial sum is an
 // integer below 2^24 and the accumulation is exact (checked on the device against int64).
 //
-// One CTA per SM, persistent over a tile list; 12 warps, 3 per scheduler partition:
+// One CTA per SM, persistent over a tile list:
 //   warp 0       producer: cp.async.bulk of pre-tiled digit planes into a ring of shared-memory stages
 //   warp 1       TMEM owner and single-thread MMA issuer; diagonal g = t+u (0-based) of the slice
 //                grid accumulates into its own TMEM buffer (BN columns), A reused through the
 //                collector across the u loop; a buffer whose group is full is handed to the
 //                epilogue ("drain": one tcgen05.commit) and replaced by a free one
-//   epilogue     replays the same deterministic drain/buffer schedule.  Eight owners of exact running
-//                sums (32 columns of 32 rows each) read each drained buffer, add q * 256^(s-1-g)
-//                into their sums, then round once to FP64 scaled by 2^(ea+eb-8s-6), apply
-//                alpha/beta, store (and for the row-table mode record a per-row |max| for the next
-//                slicing).  A warp may read only the TMEM lane quarter of its partition, and the
-//                issuer's partition is kept free of the exact arithmetic: there warp 5 only loads
-//                lane quarter 1 and hands it to its two owners on partitions 2 and 3 through
-//                shared memory (warp 9 idles).
-// CTA pairs (gemm_kernel<true>, clusters of two CTAs on two SMs): one tile is 256 x 64; each CTA
+//   epilogue     replays the same deterministic drain/buffer schedule: owner warps of exact running
+//                sums read each drained buffer, add q * 256^(s-1-g) into their sums, then round
+//                once to FP64 scaled by 2^(ea+eb-8s-6), apply alpha/beta, store (and for the
+//                row-table mode record a per-row |max| for the next slicing).  Two layouts, chosen
+//                per launch (gemm_kernel<PAIR, HO>, see EpiCfg): 16 owners of 16 columns, or 8 owners
+//                of 32 columns with the MMA issuer's scheduler partition kept free of the exact
+//                arithmetic (a loader warp hands TMEM lane quarter 1 to owners elsewhere).
+// CTA pairs (gemm_kernel<true, false>, clusters of two CTAs on two SMs): one tile is 256 x 64; each CTA
 // loads its own 128 A rows and one 32-row half of the 64 B^T rows (the operand stores the halves of
 // each k-block apart), the first CTA's thread issues cta_group::2 MMAs of M = 256 for both (each CTA
 // accumulates its 128 rows in its own TMEM), commits signal the barriers of both CTAs, the second
